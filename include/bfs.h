@@ -1,0 +1,191 @@
+/*
+ * bfs.h - C ABI of the GB300 breadth-first-search library (libbfs.so).
+ *
+ * The library computes BFS distances on an undirected graph stored as CSR
+ * (every edge present in both directions), following "Performance-Driven
+ * Optimization of Parallel Breadth-First Search" (Bhaskar, Kanakagiri, 2025):
+ * level-synchronous BFS (Section 2, Listing 1) with hybrid top-down /
+ * bottom-up traversal (Section 2, BFS-Hybrid, Listing 2), a visited bitmap
+ * (Section 2, BFS-VisitedBitmap, Listing 3) and plain, non-atomic distance
+ * stores (Section 2, BFS-NonAtomic).  The distance of a vertex is the number
+ * of edges on a shortest path from the source, the unique value every one of
+ * those variants computes.
+ *
+ * Conventions for every entry point:
+ *  - Return value: BFS_OK (0) or a negative BFS_E* code; bfs_strerror()
+ *    names it.  No C++ exception crosses this boundary.
+ *  - Vertex ids are int32 in [0, n); n < 2^31.
+ *  - Unreachable vertices get distance -1 (int32 output) or 255 (uint8
+ *    output); the paper's MAX_DISTANCE sentinel (Listing 1) maps to these.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is ordered on that stream.
+ *  - Device pointers are plain CUDA device addresses (e.g. a torch tensor's
+ *    data_ptr()) on the current device; host pointers are ordinary process
+ *    memory (pinned memory makes copies faster but is not required).
+ *  - The library owns what it allocates (graphs, workspaces, servers) until
+ *    the matching *_free / *_destroy call; the caller owns every buffer it
+ *    passes in.
+ */
+#ifndef GB300_BFS_H
+#define GB300_BFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define BFS_OK 0
+#define BFS_EINVAL (-1)   /* bad argument: null pointer, n out of range, bad CSR, src outside [0,n), k <= 0 */
+#define BFS_ENOMEM (-2)   /* device or host allocation failed, or a memory budget is exceeded */
+#define BFS_ECUDA (-3)    /* a CUDA runtime call failed (the CUDA error is logged to stderr) */
+#define BFS_ETIMEOUT (-4) /* a bounded device-side wait (grid barrier) reached its time limit */
+#define BFS_EAGAIN (-5)   /* a queue is full; retry later */
+#define BFS_ERANGE (-6)   /* a distance does not fit the requested output type (uint8: > 254) */
+#define BFS_ENOTFOUND (-7) /* unknown ticket or graph id */
+
+/* ---- bfs_graph_upload flags ---- */
+#define BFS_HOST_PTRS 0        /* row_ptr / col_idx are host pointers (copied to the device) */
+#define BFS_DEVICE_PTRS 1      /* row_ptr / col_idx are device pointers (copied device-to-device) */
+#define BFS_VALIDATE 2         /* check row_ptr[0]==0, monotone row_ptr, row_ptr[n]==m, 0<=col<n */
+#define BFS_VALIDATE_SYMMETRY 4 /* also check that every arc (u,v) has its reverse (v,u) */
+
+/* ---- direction policies (bfs_params.policy) ----
+ * Every policy yields the same distances; they differ only in work.
+ * Level 0 is always top-down (Listing 2 starts with is_top_down = true). */
+#define BFS_POLICY_AUTO 0     /* graph class rule of Section 3: average degree m/n below
+                                 bfs_params.large_diameter_degree (7) -> top-down only,
+                                 otherwise BFS_POLICY_EDGES */
+#define BFS_POLICY_FRONTIER 1 /* the paper's BFS-Hybrid rule (Section 2, Listing 2): next level
+                                 is top-down iff tau_inv*|F| < n (the paper's 5%: tau_inv = 20) */
+#define BFS_POLICY_EDGES 2    /* the edge-count rule the paper cites as BFS-Hybrid-dagger
+                                 (Section 2): top-down -> bottom-up when alpha*m_f > m_u;
+                                 bottom-up -> top-down when beta*|F| < n and |F| shrank */
+#define BFS_POLICY_TD_ONLY 3  /* top-down every level (the paper's large-diameter path, Section 3) */
+#define BFS_POLICY_BU_FROM_1 4 /* top-down at level 0, bottom-up afterwards (testing) */
+#define BFS_POLICY_SCRIPT 5   /* level L is bottom-up iff bit min(L,63) of bfs_params.script is set
+                                 (bit 0 is ignored: level 0 is top-down); testing */
+
+/* ---- launch modes (bfs_params.launch) ---- */
+#define BFS_LAUNCH_PERSISTENT 0 /* one cooperative launch runs every level, grid barrier between levels */
+#define BFS_LAUNCH_PER_LEVEL 1  /* one launch per phase; the host reads the frontier size each level */
+#define BFS_LAUNCH_GRAPH 2      /* the persistent launch replayed from a captured CUDA graph */
+
+typedef struct bfs_graph bfs_graph; /* opaque; owned by the library */
+
+/* Tunable parameters.  bfs_params_default() fills the defaults; a zero field
+ * keeps the default where noted. */
+typedef struct bfs_params {
+    int32_t policy;          /* BFS_POLICY_* (default BFS_POLICY_AUTO) */
+    int32_t launch;          /* BFS_LAUNCH_* (default BFS_LAUNCH_PERSISTENT) */
+    int32_t alpha;           /* BFS_POLICY_EDGES alpha (default 14) */
+    int32_t beta;            /* BFS_POLICY_EDGES beta (default 24) */
+    int32_t tau_inv;         /* BFS_POLICY_FRONTIER: top-down iff tau_inv*|F| < n (default 20) */
+    int32_t large_diameter_degree; /* BFS_POLICY_AUTO threshold on m/n (default 7) */
+    int32_t small_max;       /* top-down: vertices with degree < small_max (<= 32) are expanded
+                                32 at a time by one warp; larger ones get a warp each (default 32) */
+    int32_t chunk;           /* top-down: a vertex's adjacency is split into work items of at most
+                                `chunk` edges (256..65535, default 4096) */
+    int32_t bu_warp_min;     /* bottom-up: an unvisited vertex with degree > bu_warp_min is scanned by
+                                the whole warp instead of one lane (default 32) */
+    int32_t threads_per_block; /* 128..1024, multiple of 32 (default 512) */
+    int32_t blocks_per_sm;   /* 0 = as many as fit (cooperative launch limit) */
+    int32_t timeout_ms;      /* limit of every device-side barrier wait (default 10000) */
+    uint64_t script;         /* BFS_POLICY_SCRIPT direction bits */
+    int32_t test_barrier_extra; /* testing only: grid barriers wait for this many blocks more than
+                                   were launched, so a wait runs out and BFS_ETIMEOUT is returned */
+    int32_t reserved[9];
+} bfs_params;
+
+/* Per-query work counters (exact, deterministic: the frontier sets are unique
+ * and the bottom-up scan stops at the first frontier neighbour in CSR order).
+ * Edge counts are directed CSR entries. */
+typedef struct bfs_stats {
+    int32_t levels;          /* levels processed (eccentricity of src + 1) */
+    int32_t td_levels;       /* of which top-down */
+    int32_t bu_levels;       /* of which bottom-up */
+    int32_t conversions;     /* queue <-> bitmap conversions (direction changes) */
+    int64_t reached;         /* vertices with dist >= 0 */
+    int64_t edges_reached;   /* sum of degrees over reached vertices (TEPS numerator x 2) */
+    int64_t td_frontier;     /* sum over top-down levels of |F_L| */
+    int64_t td_edges;        /* sum over top-down levels of the degrees in F_L */
+    int64_t bu_unvisited;    /* sum over bottom-up levels of unvisited vertices of degree > 0 */
+    int64_t bu_edges;        /* sum over bottom-up levels of entries examined (to the first hit) */
+    int64_t bu_found;        /* sum over bottom-up levels of |F_{L+1}| */
+    int64_t conv_frontier;   /* sum over conversions of |F| */
+    int64_t reserved[4];
+} bfs_stats;
+
+/* One level's counters (optional detail). direction: 0 top-down, 1 bottom-up. */
+typedef struct bfs_level_stat {
+    int32_t direction;
+    int32_t converted;       /* 1 if this level's frontier was converted before it ran */
+    int64_t frontier;        /* |F_L| */
+    int64_t edges;           /* top-down: degrees in F_L; bottom-up: entries examined */
+    int64_t unvisited;       /* bottom-up: unvisited vertices of degree > 0 (0 for top-down) */
+    int64_t found;           /* |F_{L+1}| */
+} bfs_level_stat;
+
+/* Message for a BFS_* code (static string). */
+const char *bfs_strerror(int code);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int bfs_version(void);
+
+/* Fill *p with the defaults listed in bfs_params. */
+void bfs_params_default(bfs_params *p);
+
+/*
+ * Copy a CSR graph to the current device (Section 2, Listing 1: rptr/col).
+ *  row_ptr      n+1 offsets, int32 (row_ptr_bits = 32) or int64 (64); the
+ *               device copy keeps this width.
+ *  col_idx      m int32 neighbour ids.
+ *  flags        BFS_HOST_PTRS or BFS_DEVICE_PTRS, optionally | BFS_VALIDATE
+ *               (| BFS_VALIDATE_SYMMETRY).
+ *  out          receives the graph handle.
+ * The graph must be symmetric: the bottom-up phase (Listing 2) reads a
+ * vertex's adjacency as its in-neighbours.  Self-loops and repeated entries
+ * are allowed and do not change any distance.
+ * Errors: BFS_EINVAL (null pointers, n < 1, n >= 2^31, m < 0, int32 offsets
+ * with m >= 2^31, failed validation), BFS_ENOMEM, BFS_ECUDA.  Synchronous.
+ */
+int bfs_graph_upload(const void *row_ptr, int row_ptr_bits, const int32_t *col_idx, int64_t n,
+                     int64_t m, int flags, bfs_graph **out);
+
+/* Release a graph and its workspaces (NULL is ignored).  Synchronizes the device. */
+void bfs_graph_free(bfs_graph *g);
+
+/* Graph facts: vertex and entry counts, maximum degree, vertices of degree 0.
+ * Any output pointer may be NULL. */
+int bfs_graph_info(const bfs_graph *g, int64_t *n, int64_t *m, int64_t *max_degree,
+                   int64_t *isolated);
+
+/*
+ * Single-source BFS distances (Section 2: BFS-Hybrid with BFS-VisitedBitmap
+ * and non-atomic distance stores), default parameters.
+ *  src    source vertex in [0, n).
+ *  dist   int32[n], device or host memory (detected).  Device output is
+ *         written in stream order; host output is copied back before return.
+ * Blocks until the query has finished (the device status word is read back).
+ * Queries on one graph are serialized on the device (they share its workspace).
+ * Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ETIMEOUT.
+ */
+int bfs_single(bfs_graph *g, int32_t src, int32_t *dist, void *stream);
+
+/*
+ * bfs_single with explicit parameters and optional counters.
+ *  params       NULL = defaults.
+ *  stats        NULL, or receives the query's totals.
+ *  levels       NULL, or an array of level_cap entries receiving per-level
+ *               counters for levels 0..min(levels, level_cap)-1.
+ */
+int bfs_single_ex(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *params,
+                  bfs_stats *stats, bfs_level_stat *levels, int32_t level_cap, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_BFS_H */

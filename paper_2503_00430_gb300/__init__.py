@@ -1,0 +1,255 @@
+"""GB300 breadth-first search: thin Python binding of ``libbfs.so``.
+
+The functions here only marshal arguments for the C ABI declared in
+``include/bfs.h`` (same names); every step of the BFS runs in the library's
+CUDA kernels.  There is no CPU fallback: if ``libbfs.so`` is missing or
+cannot be loaded, every call raises.
+
+Device buffers may be passed as torch CUDA tensors (their ``data_ptr()``),
+host buffers as numpy arrays; streams as ``torch.cuda.Stream`` objects, raw
+``cudaStream_t`` integers or ``None`` (legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbfs.so")
+
+BFS_OK = 0
+BFS_EINVAL = -1
+BFS_ENOMEM = -2
+BFS_ECUDA = -3
+BFS_ETIMEOUT = -4
+BFS_EAGAIN = -5
+BFS_ERANGE = -6
+BFS_ENOTFOUND = -7
+
+BFS_HOST_PTRS = 0
+BFS_DEVICE_PTRS = 1
+BFS_VALIDATE = 2
+BFS_VALIDATE_SYMMETRY = 4
+
+BFS_POLICY_AUTO = 0
+BFS_POLICY_FRONTIER = 1
+BFS_POLICY_EDGES = 2
+BFS_POLICY_TD_ONLY = 3
+BFS_POLICY_BU_FROM_1 = 4
+BFS_POLICY_SCRIPT = 5
+
+BFS_LAUNCH_PERSISTENT = 0
+BFS_LAUNCH_PER_LEVEL = 1
+BFS_LAUNCH_GRAPH = 2
+
+
+class BfsError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = bfs_strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+class bfs_params(ctypes.Structure):
+    _fields_ = [
+        ("policy", ctypes.c_int32), ("launch", ctypes.c_int32), ("alpha", ctypes.c_int32),
+        ("beta", ctypes.c_int32), ("tau_inv", ctypes.c_int32), ("large_diameter_degree", ctypes.c_int32),
+        ("small_max", ctypes.c_int32), ("chunk", ctypes.c_int32), ("bu_warp_min", ctypes.c_int32),
+        ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+        ("timeout_ms", ctypes.c_int32), ("script", ctypes.c_uint64),
+        ("test_barrier_extra", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9),
+    ]
+
+
+class bfs_stats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32), ("td_levels", ctypes.c_int32), ("bu_levels", ctypes.c_int32),
+        ("conversions", ctypes.c_int32), ("reached", ctypes.c_int64), ("edges_reached", ctypes.c_int64),
+        ("td_frontier", ctypes.c_int64), ("td_edges", ctypes.c_int64), ("bu_unvisited", ctypes.c_int64),
+        ("bu_edges", ctypes.c_int64), ("bu_found", ctypes.c_int64), ("conv_frontier", ctypes.c_int64),
+        ("reserved", ctypes.c_int64 * 4),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class bfs_level_stat(ctypes.Structure):
+    _fields_ = [
+        ("direction", ctypes.c_int32), ("converted", ctypes.c_int32), ("frontier", ctypes.c_int64),
+        ("edges", ctypes.c_int64), ("unvisited", ctypes.c_int64), ("found", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+# (name, restype, argtypes) of every entry point the binding declares.
+_vp, _i32, _i64, _u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+_SIGNATURES = [
+    ("bfs_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("bfs_version", ctypes.c_int, []),
+    ("bfs_params_default", None, [ctypes.POINTER(bfs_params)]),
+    ("bfs_graph_upload", ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
+    ("bfs_graph_free", None, [_vp]),
+    ("bfs_graph_info", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    ("bfs_single", ctypes.c_int, [_vp, _i32, _vp, _vp]),
+    ("bfs_single_ex", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_stats),
+                                     _vp, _i32, _vp]),
+]
+
+
+def load(path: str | None = None):
+    """Load ``libbfs.so`` (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB_PATH
+        if not os.path.exists(path):
+            raise ImportError(f"libbfs.so not built ({path}); run paper_2503_00430_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_names() -> list[str]:
+    return [n for n, _, _ in _SIGNATURES]
+
+
+def _check(rc: int, what: str):
+    if rc != BFS_OK:
+        raise BfsError(rc, what)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    h = getattr(stream, "cuda_stream", None)
+    if h is not None:
+        return int(h)
+    raise TypeError("stream must be None, an int cudaStream_t or a torch.cuda.Stream")
+
+
+def _ptr(buf) -> int:
+    """Address of a torch tensor (data_ptr) or a numpy array."""
+    if hasattr(buf, "data_ptr"):
+        return int(buf.data_ptr())
+    if isinstance(buf, np.ndarray):
+        return int(buf.ctypes.data)
+    if isinstance(buf, int):
+        return buf
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def bfs_strerror(code: int) -> str:
+    return load().bfs_strerror(code).decode()
+
+
+def bfs_version() -> int:
+    return int(load().bfs_version())
+
+
+def bfs_params_default() -> bfs_params:
+    p = bfs_params()
+    load().bfs_params_default(ctypes.byref(p))
+    return p
+
+
+def make_params(**kw) -> bfs_params:
+    """Default parameters with the given fields replaced."""
+    p = bfs_params_default()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"bfs_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+class Graph:
+    """A CSR graph resident on the current CUDA device (``bfs_graph*``)."""
+
+    def __init__(self, handle: int, n: int, m: int):
+        self.handle = handle
+        self.n = n
+        self.m = m
+
+    def info(self) -> dict:
+        n, m, mx, iso = (ctypes.c_int64() for _ in range(4))
+        _check(load().bfs_graph_info(self.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(mx),
+                                     ctypes.byref(iso)), "bfs_graph_info")
+        return {"n": n.value, "m": m.value, "max_degree": mx.value, "isolated": iso.value}
+
+    def free(self):
+        if self.handle:
+            load().bfs_graph_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def bfs_graph_upload(row_ptr, col_idx, n: int | None = None, m: int | None = None, flags: int = 0,
+                     row_ptr_bits: int | None = None) -> Graph:
+    """Upload a CSR graph.  numpy arrays are host pointers, torch CUDA tensors device pointers."""
+    lib = load()
+    is_dev = hasattr(row_ptr, "is_cuda") and row_ptr.is_cuda
+    if not is_dev:
+        row_ptr = np.ascontiguousarray(row_ptr)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        if row_ptr.dtype not in (np.int32, np.int64):
+            row_ptr = row_ptr.astype(np.int64)
+        bits = row_ptr.dtype.itemsize * 8
+    else:
+        bits = row_ptr.element_size() * 8
+        flags |= BFS_DEVICE_PTRS
+    if row_ptr_bits is not None and row_ptr_bits != bits:
+        if is_dev:
+            raise ValueError("convert device row_ptr to the requested width first")
+        row_ptr = row_ptr.astype(np.int32 if row_ptr_bits == 32 else np.int64)
+        bits = row_ptr_bits
+    n = len(row_ptr) - 1 if n is None else n
+    m = len(col_idx) if m is None else m
+    h = ctypes.c_void_p()
+    _check(lib.bfs_graph_upload(_ptr(row_ptr), bits, _ptr(col_idx) if m else None, n, m, flags, ctypes.byref(h)),
+           "bfs_graph_upload")
+    return Graph(h.value, n, m)
+
+
+def bfs_graph_free(g: Graph):
+    g.free()
+
+
+def bfs_single(g: Graph, src: int, dist, stream=None):
+    """Distances from ``src`` into ``dist`` (int32[n], device tensor or host numpy array)."""
+    _check(load().bfs_single(g.handle, int(src), _ptr(dist), _stream_handle(stream)), "bfs_single")
+    return dist
+
+
+def bfs_single_ex(g: Graph, src: int, dist, params: bfs_params | None = None, stats: bool = False,
+                  level_cap: int = 0, stream=None):
+    """bfs_single with parameters; returns (stats dict or None, list of level dicts)."""
+    st = bfs_stats() if (stats or level_cap > 0) else None
+    lv = (bfs_level_stat * level_cap)() if level_cap > 0 else None
+    rc = load().bfs_single_ex(g.handle, int(src), _ptr(dist), ctypes.byref(params) if params is not None else None,
+                              ctypes.byref(st) if st is not None else None,
+                              ctypes.cast(lv, ctypes.c_void_p) if lv is not None else None, level_cap,
+                              _stream_handle(stream))
+    _check(rc, "bfs_single_ex")
+    levels = [lv[i].as_dict() for i in range(min(st.levels, level_cap))] if lv is not None else []
+    return (st.as_dict() if st is not None else None), levels

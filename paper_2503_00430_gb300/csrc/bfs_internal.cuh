@@ -1,0 +1,144 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "bfs.h"
+
+namespace gbfs {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Counters of one frontier F_L, kept in a ring of four slots indexed by L & 3.
+struct Slot {
+  unsigned long long items;  // low 32 bits: small work items, high 32 bits: large work items
+  unsigned long long nv;     // |F_L|
+  unsigned long long mf;     // sum of degrees over F_L
+  unsigned long long nq;     // vertex-queue entries written by a bitmap -> queue conversion
+};
+
+// Device control block of one single-source query (zeroed before each launch).
+struct Ctrl {
+  unsigned long long barrier;  // grid-barrier arrival counter
+  int status;                  // BFS_OK or BFS_ETIMEOUT
+  int levels, td_levels, bu_levels, conversions;
+  int pad[3];
+  unsigned long long reached, edges_reached;
+  unsigned long long td_frontier, td_edges, bu_unvisited, bu_edges, bu_found, conv_frontier;
+  Slot slot[4];
+};
+
+// Arguments of the single-source kernels (passed by value).
+struct KParams {
+  const void* rp;            // int32 or int64 row pointers [n+1]
+  const int* col;            // neighbour ids, padded with >= 4 spare entries
+  long long n, m;
+  int nw;                    // bitmap words = ceil(n / 32)
+  int src;
+  const unsigned* init_vis;  // degree-0 vertices and padding bits set
+  int* dist;
+  unsigned* vis;
+  unsigned* bm0;
+  unsigned* bm1;
+  int* qv0;
+  int* qv1;
+  unsigned long long* it0;
+  unsigned long long* it1;
+  long long cap;             // entries of it0 / it1
+  Ctrl* ctrl;
+  bfs_level_stat* lst;
+  int lst_cap;
+  int policy, alpha, beta, tau_inv;
+  unsigned long long script;
+  int small_max, chunk, bu_warp_min;
+  int need_qv;
+  long long timeout_ns;
+  int barrier_extra;
+};
+
+// Direction of level `next_level` (true = top-down), from the counters of the
+// frontier F_{next} that level next_level-1 produced.  Used identically by the
+// device (persistent kernel) and the host (per-level launches).
+//   nf_next   |F_next|          nf_cur  |F_{next-1}|
+//   mf_next   degrees in F_next m_unvisited  entries of vertices not yet visited
+__host__ __device__ inline bool next_is_top_down(int policy, int alpha, int beta, int tau_inv,
+                                                 unsigned long long script, int next_level,
+                                                 bool cur_td, long long nf_next, long long nf_cur,
+                                                 long long mf_next, long long m_unvisited,
+                                                 long long n) {
+  if (next_level == 0) return true;
+  switch (policy) {
+    case BFS_POLICY_TD_ONLY:
+      return true;
+    case BFS_POLICY_BU_FROM_1:
+      return false;
+    case BFS_POLICY_SCRIPT: {
+      int b = next_level < 63 ? next_level : 63;
+      return ((script >> b) & 1ull) == 0;
+    }
+    case BFS_POLICY_FRONTIER:
+      // Listing 2: is_top_down = cfsz < 0.05 * N, as the exact integer test tau_inv*|F| < n.
+      return (long long)tau_inv * nf_next < n;
+    case BFS_POLICY_EDGES:
+    default:
+      if (cur_td) return !((long long)alpha * mf_next > m_unvisited);
+      return (long long)beta * nf_next < n && nf_next < nf_cur;
+  }
+}
+
+// Host-side graph object.
+struct SingleWs {
+  bool ready = false;
+  unsigned* vis = nullptr;
+  unsigned* bm[2] = {nullptr, nullptr};
+  int* qv[2] = {nullptr, nullptr};
+  unsigned long long* it[2] = {nullptr, nullptr};
+  long long cap = 0;
+  Ctrl* ctrl = nullptr;       // device
+  Ctrl* h_ctrl = nullptr;     // pinned host mirror
+  Slot* h_slot = nullptr;     // pinned, per-level launch mode
+  int* dist_tmp = nullptr;    // device staging for host-memory output
+  bfs_level_stat* lst = nullptr;
+  int lst_cap = 0;
+  cudaEvent_t done = nullptr;  // last query's completion on the device
+  cudaGraph_t graph = nullptr;     // captured persistent launch (BFS_LAUNCH_GRAPH)
+  cudaGraphNode_t knode = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int gkey = -1;
+};
+
+}  // namespace gbfs
+
+struct bfs_graph {
+  long long n = 0, m = 0;
+  int rp_bits = 64;
+  int nw = 0;
+  int device = 0;
+  int num_sms = 0;
+  void* rp = nullptr;         // device row pointers
+  int* col = nullptr;         // device neighbour ids (padded)
+  unsigned* init_vis = nullptr;
+  long long max_deg = 0, isolated = 0;
+  std::mutex mu;
+  gbfs::SingleWs ws;
+};
+
+namespace gbfs {
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+#define GBFS_CUDA(call)                                                           \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) return ::gbfs::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+bool is_device_pointer(const void* p);
+int ensure_single_ws(bfs_graph* g);
+void free_single_ws(bfs_graph* g);
+int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
+               bfs_level_stat* levels, int level_cap, cudaStream_t stream);
+
+}  // namespace gbfs

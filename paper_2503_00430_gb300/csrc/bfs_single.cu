@@ -1,0 +1,895 @@
+// Single-source hybrid BFS on sm_103a.
+//
+// One query runs either as ONE persistent cooperative launch (every level,
+// grid barrier between phases) or as one launch per phase with the host
+// reading the frontier size after each level.  Both use the same device phase
+// functions below.
+//
+// Paper mapping (Section 2):
+//   * top-down level  = Listing 1's frontier loop with the visited test of
+//     Listing 3: a neighbour whose visited bit is clear is claimed with one
+//     atomicOr on its bitmap word (a bit-packed set cannot take the paper's
+//     plain `visited_bm[dst] = true`: two plain read-modify-writes of one word
+//     can lose a bit), then dist is written with a plain store;
+//   * bottom-up level = Listing 2/3: every unvisited vertex scans its
+//     adjacency in CSR order and stops at the first neighbour in the frontier
+//     bitmap; one warp owns 32 consecutive vertices, so the new frontier and
+//     visited words are built with a ballot and stored plainly;
+//   * direction switch = Listing 2's rule (or the edge-count rule it cites),
+//     queue <-> bitmap conversion on a change of direction.
+// GPU-specific pieces: the frontier is stored as edge-range work items binned
+// by degree when a vertex is discovered (small vertices 32 per warp, larger
+// ones one warp per <= chunk edges), neighbour lists are read with 128-bit
+// loads, and queue appends are aggregated per warp.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "bfs_internal.cuh"
+
+namespace gbfs {
+
+namespace {
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned r;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <typename RP>
+__device__ __forceinline__ long long rp_at(const void* rp, long long i) {
+  return (long long)__ldg(reinterpret_cast<const RP*>(rp) + i);
+}
+
+__device__ __forceinline__ int warp_incl_scan(int x) {
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long pack_item(long long start, int len) {
+  return ((unsigned long long)start << 16) | (unsigned long long)(unsigned)len;
+}
+
+// Bounded grid barrier.  Returns false when the query must stop (a wait ran
+// out of time here or elsewhere); then the status word holds BFS_ETIMEOUT.
+__device__ bool grid_barrier(const KParams& P, unsigned& epoch) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    const unsigned long long nb = (unsigned long long)gridDim.x + (unsigned long long)P.barrier_extra;
+    const unsigned long long target = (unsigned long long)epoch * nb;
+    red_release_add(&P.ctrl->barrier, 1ull);
+    int ok = 1;
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    while (ld_acquire_u64(&P.ctrl->barrier) < target) {
+      if (ld_relaxed_s32(&P.ctrl->status) != 0) {
+        ok = 0;
+        break;
+      }
+      if ((++spins & 63u) == 0) {
+        unsigned long long t = globaltimer_ns();
+        if (t0 == 0) {
+          t0 = t;
+        } else if ((long long)(t - t0) > P.timeout_ns) {
+          atomicCAS(&P.ctrl->status, 0, BFS_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && ld_relaxed_s32(&P.ctrl->status) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Per-thread work counters of one phase.
+struct Acc {
+  unsigned long long found = 0, mf = 0;        // bottom-up discoveries
+  unsigned long long edges = 0, unvisited = 0;  // statistics
+};
+
+// Block-reduce (found, mf, edges, unvisited) and add them to the level's
+// counters with one atomic per block.
+template <bool STATS>
+__device__ void flush_acc(const KParams& P, int L, Acc& a, Slot* out, bool bottom_up) {
+  __shared__ unsigned long long s_red[4][32];
+  unsigned long long v0 = warp_sum_u64(a.found), v1 = warp_sum_u64(a.mf);
+  unsigned long long v2 = STATS ? warp_sum_u64(a.edges) : 0ull;
+  unsigned long long v3 = STATS ? warp_sum_u64(a.unvisited) : 0ull;
+  const unsigned w = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  if (lane_id() == 0) {
+    s_red[0][w] = v0;
+    s_red[1][w] = v1;
+    s_red[2][w] = v2;
+    s_red[3][w] = v3;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long r[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[k] = warp_sum_u64(threadIdx.x < nwb ? s_red[k][threadIdx.x] : 0ull);
+    if (threadIdx.x == 0) {
+      if (bottom_up) {
+        if (r[0]) atomicAdd(&out->nv, r[0]);
+        if (r[1]) atomicAdd(&out->mf, r[1]);
+      }
+      if (STATS) {
+        if (bottom_up) {
+          atomicAdd(&P.ctrl->bu_edges, r[2]);
+          atomicAdd(&P.ctrl->bu_unvisited, r[3]);
+        } else {
+          atomicAdd(&P.ctrl->td_edges, r[2]);
+        }
+        if (P.lst && L < P.lst_cap) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&P.lst[L].edges), r[2]);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&P.lst[L].unvisited), r[3]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  a = Acc();
+}
+
+// ---------------------------------------------------------------- init
+
+// dist[:] = -1 except dist[src] = 0; visited = degree-0/padding mask | src bit.
+template <typename RP>
+__device__ void init_phase(const KParams& P) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long n = P.n;
+  if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
+    int4* d4 = reinterpret_cast<int4*>(P.dist);
+    const long long n4 = n >> 2;
+    for (long long i = tid; i < n4; i += nth) {
+      int4 v = make_int4(-1, -1, -1, -1);
+      if ((long long)(P.src >> 2) == i) {
+        int k = P.src & 3;
+        if (k == 0) v.x = 0;
+        if (k == 1) v.y = 0;
+        if (k == 2) v.z = 0;
+        if (k == 3) v.w = 0;
+      }
+      d4[i] = v;
+    }
+    for (long long i = (n4 << 2) + tid; i < n; i += nth) P.dist[i] = (i == P.src) ? 0 : -1;
+  } else {
+    for (long long i = tid; i < n; i += nth) P.dist[i] = (i == P.src) ? 0 : -1;
+  }
+  const int sw = P.src >> 5;
+  for (long long w = tid; w < P.nw; w += nth) {
+    unsigned x = __ldg(P.init_vis + w);
+    if (w == sw) x |= 1u << (P.src & 31);
+    P.vis[w] = x;
+  }
+}
+
+// Level-0 frontier {src}: vertex queue, work items and counters of slot 0.
+template <typename RP>
+__device__ void seed_phase(const KParams& P) {
+  const long long s = rp_at<RP>(P.rp, P.src);
+  const long long d = rp_at<RP>(P.rp, (long long)P.src + 1) - s;
+  Slot* sl = &P.ctrl->slot[0];
+  P.qv0[0] = P.src;
+  unsigned long long nsm = 0, nlg = 0;
+  if (d > 0 && d < P.small_max) {
+    P.it0[0] = pack_item(s, (int)d);
+    nsm = 1;
+  } else if (d >= P.small_max) {
+    for (long long c = 0; c * P.chunk < d; ++c) {
+      long long len = d - c * P.chunk;
+      if (len > P.chunk) len = P.chunk;
+      P.it0[P.cap - 1 - nlg] = pack_item(s + c * P.chunk, (int)len);
+      ++nlg;
+    }
+  }
+  sl->items = nsm | (nlg << 32);
+  sl->nv = 1;
+  sl->mf = (unsigned long long)d;
+}
+
+// ---------------------------------------------------------------- top-down
+
+// Warp-collective: visit neighbour u (u < 0: none) at level L.  A clear
+// visited bit is claimed with atomicOr; the claiming lane stores dist and the
+// warp appends the new vertices (vertex queue and degree-binned work items).
+template <typename RP>
+__device__ __forceinline__ void td_visit(const KParams& P, int L, int u, Slot* out, int* qvn,
+                                         unsigned long long* itn) {
+  bool claimed = false;
+  if (u >= 0) {
+    unsigned* wp = P.vis + (u >> 5);
+    const unsigned bit = 1u << (u & 31);
+    if (!(ld_relaxed_u32(wp) & bit)) claimed = !(atomicOr(wp, bit) & bit);
+  }
+  const unsigned mask = __ballot_sync(kFull, claimed);
+  if (mask == 0) return;
+  long long s = 0;
+  int d = 0;
+  if (claimed) {
+    P.dist[u] = L + 1;  // single writer: the lane that set the bit
+    s = rp_at<RP>(P.rp, u);
+    d = (int)(rp_at<RP>(P.rp, (long long)u + 1) - s);
+  }
+  const unsigned lane = lane_id();
+  const int nsm = (claimed && d > 0 && d < P.small_max) ? 1 : 0;
+  const int nlg = (claimed && d >= P.small_max) ? (d + P.chunk - 1) / P.chunk : 0;
+  const unsigned smask = __ballot_sync(kFull, nsm);
+  const int lg_incl = warp_incl_scan(nlg);
+  const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
+  const unsigned long long dsum = warp_sum_u64((unsigned long long)d);
+  const int leader = __ffs(mask) - 1;
+  unsigned long long b_items = 0, b_q = 0;
+  if ((int)lane == leader) {
+    b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
+    b_q = atomicAdd(&out->nv, (unsigned long long)__popc(mask));
+    atomicAdd(&out->mf, dsum);
+  }
+  b_items = __shfl_sync(kFull, b_items, leader);
+  b_q = __shfl_sync(kFull, b_q, leader);
+  const unsigned lt = lanemask_lt();
+  if (claimed && P.need_qv) qvn[b_q + __popc(mask & lt)] = u;
+  if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
+  if (nlg) {
+    unsigned long long b = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
+    for (int c = 0; c < nlg; ++c) {
+      int len = d - c * P.chunk;
+      if (len > P.chunk) len = P.chunk;
+      itn[P.cap - 1 - (long long)(b + c)] = pack_item(s + (long long)c * P.chunk, len);
+    }
+  }
+}
+
+template <typename RP, bool STATS>
+__device__ void td_phase(const KParams& P, int L, unsigned long long items_cur) {
+  const unsigned long long nsmall = items_cur & 0xffffffffull, nlarge = items_cur >> 32;
+  const unsigned long long* it = (L & 1) ? P.it1 : P.it0;
+  unsigned long long* itn = (L & 1) ? P.it0 : P.it1;
+  int* qvn = (L & 1) ? P.qv0 : P.qv1;
+  Slot* out = &P.ctrl->slot[(L + 1) & 3];
+  const unsigned lane = lane_id();
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  Acc acc;
+  // Small items: 32 per warp, edges dealt to lanes by an exclusive scan of lengths.
+  for (long long g = gw; (unsigned long long)g * 32ull < nsmall; g += nwarps) {
+    const unsigned long long i = (unsigned long long)g * 32ull + lane;
+    const unsigned long long item = i < nsmall ? it[i] : 0ull;
+    const long long s = (long long)(item >> 16);
+    const int len = (int)(item & 0xffffull);
+    const int incl = warp_incl_scan(len);
+    const int excl = incl - len;
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (STATS) acc.edges += (unsigned long long)len;
+    for (int base = 0; base < total; base += 32) {
+      const int e = base + (int)lane;
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const int ex = __shfl_sync(kFull, excl, lo + step);
+        if (ex <= e) lo += step;
+      }
+      const long long so = __shfl_sync(kFull, s, lo);
+      const int exo = __shfl_sync(kFull, excl, lo);
+      int u = -1;
+      if (e < total) u = __ldg(P.col + so + (e - exo));
+      td_visit<RP>(P, L, u, out, qvn, itn);
+    }
+  }
+  // Large items: one warp per item, 128-bit loads of the aligned span.
+  for (long long i = gw; (unsigned long long)i < nlarge; i += nwarps) {
+    const unsigned long long item = it[P.cap - 1 - i];
+    const long long s = (long long)(item >> 16);
+    const int len = (int)(item & 0xffffull);
+    const long long e = s + len;
+    if (STATS && lane == 0) acc.edges += (unsigned long long)len;
+    for (long long base = s & ~3ll; base < e; base += 128) {
+      const long long j = base + 4 * (long long)lane;
+      int4 q = make_int4(-1, -1, -1, -1);
+      if (j < e) q = __ldg(reinterpret_cast<const int4*>(P.col + j));
+      const int c0 = (j >= s && j < e) ? q.x : -1;
+      const int c1 = (j + 1 >= s && j + 1 < e) ? q.y : -1;
+      const int c2 = (j + 2 >= s && j + 2 < e) ? q.z : -1;
+      const int c3 = (j + 3 >= s && j + 3 < e) ? q.w : -1;
+      td_visit<RP>(P, L, c0, out, qvn, itn);
+      td_visit<RP>(P, L, c1, out, qvn, itn);
+      td_visit<RP>(P, L, c2, out, qvn, itn);
+      td_visit<RP>(P, L, c3, out, qvn, itn);
+    }
+  }
+  if (STATS) flush_acc<STATS>(P, L, acc, out, false);
+}
+
+// ---------------------------------------------------------------- bottom-up
+
+__device__ __forceinline__ bool in_frontier(const unsigned* front, int u) {
+  return (front[u >> 5] >> (u & 31)) & 1u;
+}
+
+template <typename RP, bool STATS>
+__device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigned* next) {
+  Slot* out = &P.ctrl->slot[(L + 1) & 3];
+  const unsigned lane = lane_id();
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  Acc acc;
+  for (long long w = gw; w < P.nw; w += nwarps) {
+    const unsigned vis = P.vis[w];
+    if (vis == kFull) {
+      if (lane == 0) next[w] = 0u;
+      continue;
+    }
+    const long long v = w * 32 + lane;
+    const bool active = !((vis >> lane) & 1u);  // padding bits past n are set, so v < n here
+    long long s = 0, e = 0;
+    if (active) {
+      s = rp_at<RP>(P.rp, v);
+      e = rp_at<RP>(P.rp, v + 1);
+    }
+    const long long d = e - s;
+    bool found = false;
+    long long examined = 0;
+    const bool heavy = active && d > P.bu_warp_min;
+    if (active && !heavy) {
+      long long j = s, hit = -1;
+      for (; j < e && (j & 3); ++j) {
+        if (in_frontier(front, __ldg(P.col + j))) {
+          hit = j;
+          break;
+        }
+      }
+      if (hit < 0) {
+        for (; j < e; j += 4) {
+          const int4 q = __ldg(reinterpret_cast<const int4*>(P.col + j));
+          if (in_frontier(front, q.x)) { hit = j; break; }
+          if (j + 1 < e && in_frontier(front, q.y)) { hit = j + 1; break; }
+          if (j + 2 < e && in_frontier(front, q.z)) { hit = j + 2; break; }
+          if (j + 3 < e && in_frontier(front, q.w)) { hit = j + 3; break; }
+        }
+      }
+      found = hit >= 0;
+      examined = found ? hit - s + 1 : d;
+    }
+    unsigned hv = __ballot_sync(kFull, heavy);
+    while (hv) {
+      const int h = __ffs(hv) - 1;
+      hv &= hv - 1;
+      const long long hs = __shfl_sync(kFull, s, h), he = __shfl_sync(kFull, e, h);
+      bool hf = false;
+      long long hx = he - hs;
+      for (long long b = hs; b < he; b += 32) {
+        const long long j = b + lane;
+        const bool hit = j < he && in_frontier(front, __ldg(P.col + j));
+        const unsigned bm = __ballot_sync(kFull, hit);
+        if (bm) {
+          hf = true;
+          hx = (b - hs) + __ffs(bm);
+          break;
+        }
+      }
+      if ((int)lane == h) {
+        found = hf;
+        examined = hx;
+      }
+    }
+    const unsigned fm = __ballot_sync(kFull, found);
+    if (lane == 0) {
+      next[w] = fm;
+      if (fm) P.vis[w] = vis | fm;  // the owning warp is the only writer of this word
+      acc.found += (unsigned long long)__popc(fm);
+    }
+    if (found) {
+      P.dist[v] = L + 1;
+      acc.mf += (unsigned long long)d;
+    }
+    if (STATS) {
+      acc.edges += (unsigned long long)examined;
+      acc.unvisited += active ? 1ull : 0ull;
+    }
+  }
+  flush_acc<STATS>(P, L, acc, out, true);
+}
+
+// ---------------------------------------------------------------- conversions
+
+__device__ void zero_words(unsigned* p, long long nw) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long w = tid; w < nw; w += nth) p[w] = 0u;
+}
+
+// Queue -> bitmap: set the bit of every vertex of F (nv entries of qv).
+__device__ void scatter_phase(const int* qv, long long nv, unsigned* bm) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < nv; i += nth) {
+    const int v = qv[i];
+    atomicOr(bm + (v >> 5), 1u << (v & 31));
+  }
+}
+
+// Bitmap -> queue: for the frontier F_{L+1} in bitmap `bm`, write the vertex
+// queue and the degree-binned work items of parity (L+1).
+template <typename RP>
+__device__ void convert_phase(const KParams& P, int L, const unsigned* bm) {
+  const int Ln = L + 1;
+  unsigned long long* itn = (Ln & 1) ? P.it1 : P.it0;
+  int* qvn = (Ln & 1) ? P.qv1 : P.qv0;
+  Slot* out = &P.ctrl->slot[Ln & 3];
+  const unsigned lane = lane_id();
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned lt = lanemask_lt();
+  for (long long w = gw; w < P.nw; w += nwarps) {
+    const unsigned word = bm[w];
+    if (word == 0u) continue;
+    const bool mine = (word >> lane) & 1u;
+    const long long v = w * 32 + lane;
+    long long s = 0;
+    int d = 0;
+    if (mine) {
+      s = rp_at<RP>(P.rp, v);
+      d = (int)(rp_at<RP>(P.rp, v + 1) - s);
+    }
+    const int nsm = (mine && d > 0 && d < P.small_max) ? 1 : 0;
+    const int nlg = (mine && d >= P.small_max) ? (d + P.chunk - 1) / P.chunk : 0;
+    const unsigned smask = __ballot_sync(kFull, nsm);
+    const int lg_incl = warp_incl_scan(nlg);
+    const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
+    unsigned long long b_items = 0, b_q = 0;
+    if (lane == 0) {
+      b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
+      if (P.need_qv) b_q = atomicAdd(&out->nq, (unsigned long long)__popc(word));
+    }
+    b_items = __shfl_sync(kFull, b_items, 0);
+    b_q = __shfl_sync(kFull, b_q, 0);
+    if (mine && P.need_qv) qvn[b_q + __popc(word & lt)] = (int)v;
+    if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
+    if (nlg) {
+      unsigned long long b = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
+      for (int c = 0; c < nlg; ++c) {
+        int len = d - c * P.chunk;
+        if (len > P.chunk) len = P.chunk;
+        itn[P.cap - 1 - (long long)(b + c)] = pack_item(s + (long long)c * P.chunk, len);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- level loop
+
+struct LoopState {
+  int L = 0;
+  bool td = true;
+  int fb = 0;                   // bitmap index holding the frontier in bottom-up mode
+  long long nf_cur = 1;         // |F_L|
+  long long edges_visited = 0;  // degrees of all visited vertices
+  long long reached = 1;
+};
+
+template <bool STATS>
+__device__ void record_level(const KParams& P, const LoopState& st, long long found, int converted) {
+  if (STATS && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (P.lst && st.L < P.lst_cap) {
+      P.lst[st.L].direction = st.td ? 0 : 1;
+      P.lst[st.L].converted = converted;
+      P.lst[st.L].frontier = st.nf_cur;
+      P.lst[st.L].found = found;
+    }
+    if (st.td) {
+      P.ctrl->td_frontier += (unsigned long long)st.nf_cur;
+    } else {
+      P.ctrl->bu_found += (unsigned long long)found;
+    }
+  }
+}
+
+template <typename RP, bool STATS>
+__global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
+  unsigned epoch = 0;
+  init_phase<RP>(P);
+  if (blockIdx.x == 0 && threadIdx.x == 0) seed_phase<RP>(P);
+  if (!grid_barrier(P, epoch)) return;
+  LoopState st;
+  st.edges_visited = (long long)ld_relaxed_u64(&P.ctrl->slot[0].mf);
+  unsigned long long items = ld_relaxed_u64(&P.ctrl->slot[0].items);
+  int converted = 0, conversions = 0, tdl = 0, bul = 0;
+  for (;;) {
+    const int L = st.L;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      Slot* z = &P.ctrl->slot[(L + 2) & 3];
+      z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0;
+    }
+    if (st.td) {
+      ++tdl;
+      td_phase<RP, STATS>(P, L, items);
+    } else {
+      ++bul;
+      bu_phase<RP, STATS>(P, L, st.fb ? P.bm1 : P.bm0, st.fb ? P.bm0 : P.bm1);
+    }
+    if (!grid_barrier(P, epoch)) return;
+    Slot* nx = &P.ctrl->slot[(L + 1) & 3];
+    const long long nf = (long long)ld_relaxed_u64(&nx->nv);
+    const long long mf = (long long)ld_relaxed_u64(&nx->mf);
+    record_level<STATS>(P, st, nf, converted);
+    if (nf == 0) break;
+    st.edges_visited += mf;
+    st.reached += nf;
+    const bool ntd = next_is_top_down(P.policy, P.alpha, P.beta, P.tau_inv, P.script, L + 1, st.td, nf,
+                                      st.nf_cur, mf, P.m - st.edges_visited, P.n);
+    converted = 0;
+    if (st.td && !ntd) {
+      // top-down -> bottom-up: the new frontier's vertex queue becomes bitmap bm0
+      zero_words(P.bm0, P.nw);
+      if (!grid_barrier(P, epoch)) return;
+      scatter_phase(((L + 1) & 1) ? P.qv1 : P.qv0, nf, P.bm0);
+      if (!grid_barrier(P, epoch)) return;
+      st.fb = 0;
+      converted = 1;
+    } else if (!st.td && ntd) {
+      // bottom-up -> top-down: the bitmap just written becomes the queue and work items
+      convert_phase<RP>(P, L, st.fb ? P.bm0 : P.bm1);
+      if (!grid_barrier(P, epoch)) return;
+      converted = 1;
+    } else if (!st.td && !ntd) {
+      st.fb ^= 1;
+    }
+    if (converted) {
+      ++conversions;
+      if (STATS && blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->conv_frontier += (unsigned long long)nf;
+    }
+    if (ntd) items = ld_relaxed_u64(&nx->items);
+    st.td = ntd;
+    st.nf_cur = nf;
+    st.L = L + 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.ctrl->levels = st.L + 1;
+    P.ctrl->td_levels = tdl;
+    P.ctrl->bu_levels = bul;
+    P.ctrl->conversions = conversions;
+    P.ctrl->reached = (unsigned long long)st.reached;
+    P.ctrl->edges_reached = (unsigned long long)st.edges_visited;
+  }
+}
+
+// ---- per-phase kernels (BFS_LAUNCH_PER_LEVEL) ----
+
+template <typename RP>
+__global__ void __launch_bounds__(1024) k_init_seed(KParams P) {
+  init_phase<RP>(P);
+  if (blockIdx.x == 0 && threadIdx.x == 0) seed_phase<RP>(P);
+}
+
+template <typename RP, bool STATS>
+__global__ void __launch_bounds__(1024) k_level(KParams P, int L, int td, int fb, unsigned long long items) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Slot* z = &P.ctrl->slot[(L + 2) & 3];
+    z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0;
+  }
+  if (td) {
+    td_phase<RP, STATS>(P, L, items);
+  } else {
+    bu_phase<RP, STATS>(P, L, fb ? P.bm1 : P.bm0, fb ? P.bm0 : P.bm1);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_zero_words(unsigned* p, long long nw) { zero_words(p, nw); }
+
+__global__ void __launch_bounds__(1024) k_scatter(const int* qv, long long nv, unsigned* bm) {
+  scatter_phase(qv, nv, bm);
+}
+
+template <typename RP>
+__global__ void __launch_bounds__(1024) k_convert(KParams P, int L, const unsigned* bm) {
+  convert_phase<RP>(P, L, bm);
+}
+
+template <typename RP, bool STATS>
+struct Kernels {
+  static void* persistent() { return reinterpret_cast<void*>(&bfs_persistent_kernel<RP, STATS>); }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+static int resolve_policy(const bfs_graph* g, const bfs_params& p) {
+  if (p.policy != BFS_POLICY_AUTO) return p.policy;
+  // Section 3: average degree below 7 marks a large-diameter graph -> top-down only.
+  if ((double)g->m < (double)p.large_diameter_degree * (double)g->n) return BFS_POLICY_TD_ONLY;
+  return BFS_POLICY_EDGES;
+}
+
+static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, KParams& K) {
+  SingleWs& ws = g->ws;
+  K.rp = g->rp;
+  K.col = g->col;
+  K.n = g->n;
+  K.m = g->m;
+  K.nw = g->nw;
+  K.src = src;
+  K.init_vis = g->init_vis;
+  K.dist = dist;
+  K.vis = ws.vis;
+  K.bm0 = ws.bm[0];
+  K.bm1 = ws.bm[1];
+  K.qv0 = ws.qv[0];
+  K.qv1 = ws.qv[1];
+  K.it0 = ws.it[0];
+  K.it1 = ws.it[1];
+  K.cap = ws.cap;
+  K.ctrl = ws.ctrl;
+  K.lst = nullptr;
+  K.lst_cap = 0;
+  K.policy = resolve_policy(g, p);
+  K.alpha = p.alpha;
+  K.beta = p.beta;
+  K.tau_inv = p.tau_inv;
+  K.script = p.script;
+  K.small_max = p.small_max;
+  K.chunk = p.chunk;
+  K.bu_warp_min = p.bu_warp_min;
+  K.need_qv = K.policy != BFS_POLICY_TD_ONLY;
+  K.timeout_ns = (long long)p.timeout_ms * 1000000ll;
+  K.barrier_extra = p.test_barrier_extra;
+}
+
+template <typename RP, bool STATS>
+static int launch_persistent(bfs_graph* g, KParams& K, const bfs_params& p, cudaStream_t stream) {
+  void* fn = Kernels<RP, STATS>::persistent();
+  int per_sm = 0;
+  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, 0));
+  if (per_sm < 1) return BFS_EINVAL;
+  if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
+  dim3 grid((unsigned)(per_sm * g->num_sms)), block((unsigned)p.threads_per_block);
+  void* args[] = {&K};
+  GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, 0, stream));
+  return BFS_OK;
+}
+
+template <typename RP, bool STATS>
+static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaStream_t stream) {
+  SingleWs& ws = g->ws;
+  int per_sm = 0;
+  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, reinterpret_cast<void*>(&k_level<RP, STATS>), p.threads_per_block, 0));
+  if (per_sm < 1) return BFS_EINVAL;
+  if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
+  dim3 grid((unsigned)(per_sm * g->num_sms)), block((unsigned)p.threads_per_block);
+  k_init_seed<RP><<<grid, block, 0, stream>>>(K);
+  GBFS_CUDA(cudaGetLastError());
+  GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[0], sizeof(Slot), cudaMemcpyDeviceToHost, stream));
+  GBFS_CUDA(cudaStreamSynchronize(stream));
+  long long edges_visited = (long long)ws.h_slot->mf;
+  unsigned long long items = ws.h_slot->items;
+  long long nf_cur = 1, reached = 1;
+  int L = 0, fb = 0, tdl = 0, bul = 0, conversions = 0, converted = 0;
+  bool td = true;
+  Ctrl host_tot{};
+  for (;;) {
+    k_level<RP, STATS><<<grid, block, 0, stream>>>(K, L, td ? 1 : 0, fb, items);
+    GBFS_CUDA(cudaGetLastError());
+    if (td) ++tdl; else ++bul;
+    GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,
+                              stream));
+    GBFS_CUDA(cudaStreamSynchronize(stream));
+    const long long nf = (long long)ws.h_slot->nv, mf = (long long)ws.h_slot->mf;
+    if (STATS) {
+      if (K.lst && L < K.lst_cap) {
+        bfs_level_stat ls{};
+        GBFS_CUDA(cudaMemcpy(&ls, &K.lst[L], sizeof(ls), cudaMemcpyDeviceToHost));
+        ls.direction = td ? 0 : 1;
+        ls.converted = converted;
+        ls.frontier = nf_cur;
+        ls.found = nf;
+        GBFS_CUDA(cudaMemcpy(&K.lst[L], &ls, sizeof(ls), cudaMemcpyHostToDevice));
+      }
+      if (td) host_tot.td_frontier += (unsigned long long)nf_cur; else host_tot.bu_found += (unsigned long long)nf;
+    }
+    if (nf == 0) break;
+    edges_visited += mf;
+    reached += nf;
+    const bool ntd = next_is_top_down(K.policy, K.alpha, K.beta, K.tau_inv, K.script, L + 1, td, nf, nf_cur, mf,
+                                      K.m - edges_visited, K.n);
+    converted = 0;
+    if (td && !ntd) {
+      k_zero_words<<<grid, block, 0, stream>>>(K.bm0, K.nw);
+      k_scatter<<<grid, block, 0, stream>>>(((L + 1) & 1) ? K.qv1 : K.qv0, nf, K.bm0);
+      GBFS_CUDA(cudaGetLastError());
+      fb = 0;
+      converted = 1;
+    } else if (!td && ntd) {
+      k_convert<RP><<<grid, block, 0, stream>>>(K, L, fb ? K.bm0 : K.bm1);
+      GBFS_CUDA(cudaGetLastError());
+      GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,
+                                stream));
+      GBFS_CUDA(cudaStreamSynchronize(stream));
+      converted = 1;
+    } else if (!td && !ntd) {
+      fb ^= 1;
+    }
+    if (converted) {
+      ++conversions;
+      host_tot.conv_frontier += (unsigned long long)nf;
+    }
+    if (ntd) items = ws.h_slot->items;
+    td = ntd;
+    nf_cur = nf;
+    ++L;
+  }
+  // Write the loop's totals where the persistent kernel would have left them.
+  GBFS_CUDA(cudaStreamSynchronize(stream));
+  Ctrl c{};
+  GBFS_CUDA(cudaMemcpy(&c, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  c.levels = L + 1;
+  c.td_levels = tdl;
+  c.bu_levels = bul;
+  c.conversions = conversions;
+  c.reached = (unsigned long long)reached;
+  c.edges_reached = (unsigned long long)edges_visited;
+  c.td_frontier = host_tot.td_frontier;
+  c.bu_found = host_tot.bu_found;
+  c.conv_frontier = host_tot.conv_frontier;
+  GBFS_CUDA(cudaMemcpy(ws.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  return BFS_OK;
+}
+
+// The persistent launch (control-block reset + cooperative kernel) captured
+// once as a CUDA graph per workspace and replayed with refreshed arguments.
+template <typename RP>
+static int launch_graph(bfs_graph* g, KParams& K, const bfs_params& p, cudaStream_t stream) {
+  SingleWs& ws = g->ws;
+  void* fn = Kernels<RP, false>::persistent();
+  int per_sm = 0;
+  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, 0));
+  if (per_sm < 1) return BFS_EINVAL;
+  if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
+  cudaKernelNodeParams kp{};
+  kp.func = fn;
+  kp.gridDim = dim3((unsigned)(per_sm * g->num_sms));
+  kp.blockDim = dim3((unsigned)p.threads_per_block);
+  kp.sharedMemBytes = 0;
+  void* args[] = {&K};
+  kp.kernelParams = args;
+  const int key = (per_sm * 4096 + p.threads_per_block) * 2 + (g->rp_bits == 32 ? 1 : 0);
+  if (ws.gexec == nullptr || ws.gkey != key) {
+    if (ws.gexec) cudaGraphExecDestroy(ws.gexec);
+    if (ws.graph) cudaGraphDestroy(ws.graph);
+    ws.gexec = nullptr;
+    ws.graph = nullptr;
+    GBFS_CUDA(cudaGraphCreate(&ws.graph, 0));
+    cudaGraphNode_t memset_node;
+    cudaMemsetParams mp{};
+    mp.dst = ws.ctrl;
+    mp.value = 0;
+    mp.elementSize = 1;
+    mp.width = sizeof(Ctrl);
+    mp.height = 1;
+    mp.pitch = 0;
+    GBFS_CUDA(cudaGraphAddMemsetNode(&memset_node, ws.graph, nullptr, 0, &mp));
+    GBFS_CUDA(cudaGraphAddKernelNode(&ws.knode, ws.graph, &memset_node, 1, &kp));
+    cudaLaunchAttributeValue coop{};
+    coop.cooperative = 1;
+    GBFS_CUDA(cudaGraphKernelNodeSetAttribute(ws.knode, cudaLaunchAttributeCooperative, &coop));
+    GBFS_CUDA(cudaGraphInstantiate(&ws.gexec, ws.graph, 0));
+    ws.gkey = key;
+  } else {
+    GBFS_CUDA(cudaGraphExecKernelNodeSetParams(ws.gexec, ws.knode, &kp));
+  }
+  GBFS_CUDA(cudaGraphLaunch(ws.gexec, stream));
+  return BFS_OK;
+}
+
+int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
+               bfs_level_stat* levels, int level_cap, cudaStream_t stream) {
+  SingleWs& ws = g->ws;
+  KParams K;
+  fill_kparams(g, src, dist_dev, p, K);
+  const bool stats = st != nullptr || (levels != nullptr && level_cap > 0);
+  if (levels && level_cap > 0) {
+    if (ws.lst_cap < level_cap) {
+      if (ws.lst) cudaFree(ws.lst);
+      ws.lst = nullptr;
+      ws.lst_cap = 0;
+      GBFS_CUDA(cudaMalloc(&ws.lst, sizeof(bfs_level_stat) * (size_t)level_cap));
+      ws.lst_cap = level_cap;
+    }
+    GBFS_CUDA(cudaMemsetAsync(ws.lst, 0, sizeof(bfs_level_stat) * (size_t)level_cap, stream));
+    K.lst = ws.lst;
+    K.lst_cap = level_cap;
+  }
+  GBFS_CUDA(cudaStreamWaitEvent(stream, ws.done, 0));
+  int rc;
+  int launch = p.launch;
+  if (launch == BFS_LAUNCH_GRAPH && stats) launch = BFS_LAUNCH_PERSISTENT;
+  if (launch != BFS_LAUNCH_GRAPH) GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
+  if (launch == BFS_LAUNCH_GRAPH) {
+    rc = g->rp_bits == 32 ? launch_graph<int>(g, K, p, stream) : launch_graph<long long>(g, K, p, stream);
+  } else if (launch == BFS_LAUNCH_PER_LEVEL) {
+    if (g->rp_bits == 32)
+      rc = stats ? launch_per_level<int, true>(g, K, p, stream) : launch_per_level<int, false>(g, K, p, stream);
+    else
+      rc = stats ? launch_per_level<long long, true>(g, K, p, stream)
+                 : launch_per_level<long long, false>(g, K, p, stream);
+  } else {
+    if (g->rp_bits == 32)
+      rc = stats ? launch_persistent<int, true>(g, K, p, stream) : launch_persistent<int, false>(g, K, p, stream);
+    else
+      rc = stats ? launch_persistent<long long, true>(g, K, p, stream)
+                 : launch_persistent<long long, false>(g, K, p, stream);
+  }
+  if (rc != BFS_OK) return rc;
+  GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream));
+  GBFS_CUDA(cudaEventRecord(ws.done, stream));
+  GBFS_CUDA(cudaStreamSynchronize(stream));
+  const Ctrl& c = *ws.h_ctrl;
+  if (c.status != 0) return c.status;
+  if (st) {
+    st->levels = c.levels;
+    st->td_levels = c.td_levels;
+    st->bu_levels = c.bu_levels;
+    st->conversions = c.conversions;
+    st->reached = (int64_t)c.reached;
+    st->edges_reached = (int64_t)c.edges_reached;
+    st->td_frontier = (int64_t)c.td_frontier;
+    st->td_edges = (int64_t)c.td_edges;
+    st->bu_unvisited = (int64_t)c.bu_unvisited;
+    st->bu_edges = (int64_t)c.bu_edges;
+    st->bu_found = (int64_t)c.bu_found;
+    st->conv_frontier = (int64_t)c.conv_frontier;
+  }
+  if (levels && level_cap > 0) {
+    int nl = c.levels < level_cap ? c.levels : level_cap;
+    GBFS_CUDA(cudaMemcpy(levels, ws.lst, sizeof(bfs_level_stat) * (size_t)nl, cudaMemcpyDeviceToHost));
+  }
+  return BFS_OK;
+}
+
+}  // namespace gbfs

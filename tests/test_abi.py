@@ -1,0 +1,60 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/bfs.h (CPU only: no compute call is made)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bfs.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(bfs_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2503_00430_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("bfs_graph_upload", "bfs_graph_free", "bfs_single", "bfs_single_ex", "bfs_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches_header(lib_path):
+    import paper_2503_00430_gb300 as B
+    lib = ctypes.CDLL(lib_path)
+    for n in declared_functions():
+        assert hasattr(lib, n)
+    assert sorted(B.exported_names()) == declared_functions()
+    B.load(lib_path)
+    assert B.bfs_strerror(B.BFS_ETIMEOUT) == "device-side wait timed out"
+    p = B.bfs_params_default()
+    assert (p.alpha, p.beta, p.tau_inv, p.large_diameter_degree) == (14, 24, 20, 7)
+
+
+def test_host_only_calls_fail_cleanly_without_gpu(lib_path):
+    import paper_2503_00430_gb300 as B
+    B.load(lib_path)
+    import numpy as np
+    with pytest.raises(B.BfsError) as e:
+        B.bfs_graph_upload(np.array([0, 0], dtype=np.int64), np.zeros(0, dtype=np.int32), n=0)
+    assert e.value.code == B.BFS_EINVAL
+

@@ -1,0 +1,188 @@
+"""GPU parity of single-source BFS against the oracle (bit-exact).
+
+Distances are unique (the shortest-path hop count), so every policy, launch
+mode and parameter set must reproduce the oracle's int32 array exactly.  The
+work counters the library reports are compared with the host replay of the
+same policy on the oracle's levels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import graphs as G
+from tests.replay import replay
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bfs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_00430_gb300 as B
+    B.load()
+    return B
+
+
+POLICIES = {
+    "auto": dict(policy=0),
+    "frontier": dict(policy=1),
+    "edges": dict(policy=2),
+    "td_only": dict(policy=3),
+    "bu_from_1": dict(policy=4),
+    "script_alt": dict(policy=5, script=0xAAAAAAAAAAAAAAAA),
+    "script_rand": dict(policy=5, script=0x9D3F5A61C2E4B807),
+}
+
+
+def run(B, g, src, n, stream=None, **kw):
+    dist = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = B.make_params(**kw)
+    st, lv = B.bfs_single_ex(g, int(src), dist, params=p, stats=True, level_cap=4096, stream=stream)
+    return dist.cpu().numpy(), st, lv
+
+
+def check(B, rp, col, srcs, rp_bits=64, policies=POLICIES, launches=(0, 1), extra=None, check_stats=True):
+    g = B.bfs_graph_upload(rp, col, flags=B.BFS_VALIDATE | B.BFS_VALIDATE_SYMMETRY, row_ptr_bits=rp_bits)
+    n = len(rp) - 1
+    for src in srcs:
+        want = oracle.bfs(rp, col, int(src))
+        for name, kw in policies.items():
+            for launch in launches:
+                kw2 = dict(kw, launch=launch, **(extra or {}))
+                got, st, lv = run(B, g, src, n, **kw2)
+                assert np.array_equal(got, want), (name, launch, int(src), np.nonzero(got != want)[0][:10])
+                if check_stats:
+                    est, elv = replay(rp, col, int(src), want, policy=kw.get("policy", 0), script=kw.get("script", 0))
+                    for k, v in est.items():
+                        assert st[k] == v, (name, launch, k, st[k], v)
+                    assert lv == elv, (name, launch)
+    g.free()
+
+
+def test_closed_form_graphs(bfs):
+    cases = [G.path_graph(1), G.path_graph(2), G.path_graph(100), G.star_graph(40), G.complete_graph(9),
+             G.cycle_graph(33), graphgen.grid2d(7, 45)]
+    for rp, col in cases:
+        n = len(rp) - 1
+        check(bfs, rp, col, sorted({0, n // 2, n - 1}))
+
+
+def test_disjoint_union_and_isolated(bfs):
+    edges = [(i, i + 1) for i in range(4)] + [(5 + i, 5 + (i + 1) % 6) for i in range(6)]
+    rp, col = G.csr_from_edges(70, edges)  # vertices 11..69 isolated
+    check(bfs, rp, col, [2, 5, 11, 69])
+
+
+def test_rmat_s16_td(bfs):
+    """R-MAT scale 16, plain top-down, 8 sources, int32 row pointers."""
+    rp, col = graphgen.rmat(16)
+    srcs = graphgen.sources(rp, 8, 1001)
+    check(bfs, rp, col, srcs, rp_bits=32, policies={"td_only": dict(policy=3)}, launches=(0, 1, 2))
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_rmat_s14_all_policies(bfs, bits):
+    rp, col = graphgen.rmat(14, seed=7)
+    check(bfs, rp, col, graphgen.sources(rp, 3, 1002), rp_bits=bits)
+
+
+def test_er_and_rgg_and_grid(bfs):
+    for rp, col in (graphgen.erdos_renyi(20000, 16, 2), graphgen.rgg(30000, graphgen.rgg_radius(30000, 6.0), 3),
+                    graphgen.grid2d(150, 131)):
+        check(bfs, rp, col, graphgen.sources(rp, 2, 1003), rp_bits=32,
+              policies={k: POLICIES[k] for k in ("auto", "frontier", "edges", "script_rand")})
+
+
+@pytest.mark.parametrize("params", [
+    dict(small_max=1, chunk=256, bu_warp_min=0, threads_per_block=128),
+    dict(small_max=8, chunk=300, bu_warp_min=4, threads_per_block=1024, blocks_per_sm=1),
+    dict(small_max=32, chunk=65535, bu_warp_min=1000000, threads_per_block=256, blocks_per_sm=2),
+])
+def test_parameter_extremes(bfs, params):
+    rp, col = graphgen.rmat(13, seed=9)
+    check(bfs, rp, col, graphgen.sources(rp, 2, 1004), extra=params,
+          policies={k: POLICIES[k] for k in ("edges", "bu_from_1", "script_rand")})
+
+
+def test_hub_split_over_chunks(bfs):
+    """A star with 200,000 leaves: the hub's adjacency exceeds 65,535 and is split into chunks."""
+    rp, col = G.star_graph(200001)
+    check(bfs, rp, col, [0, 7], policies={k: POLICIES[k] for k in ("td_only", "edges", "bu_from_1")})
+
+
+def test_host_output_buffer(bfs):
+    rp, col = graphgen.rmat(12)
+    g = bfs.bfs_graph_upload(rp, col)
+    src = int(graphgen.sources(rp, 1, 5)[0])
+    host = np.full(len(rp) - 1, 77, dtype=np.int32)
+    bfs.bfs_single(g, src, host)
+    assert np.array_equal(host, oracle.bfs(rp, col, src))
+    g.free()
+
+
+def test_stream_and_repeated_queries(bfs):
+    rp, col = graphgen.rmat(13)
+    g = bfs.bfs_graph_upload(rp, col)
+    s = torch.cuda.Stream()
+    srcs = graphgen.sources(rp, 5, 8)
+    outs = []
+    for src in srcs:
+        d = torch.empty(len(rp) - 1, dtype=torch.int32, device="cuda")
+        bfs.bfs_single(g, int(src), d, stream=s)
+        outs.append(d)
+    torch.cuda.synchronize()
+    for src, d in zip(srcs, outs):
+        assert np.array_equal(d.cpu().numpy(), oracle.bfs(rp, col, int(src)))
+    g.free()
+
+
+def test_invalid_arguments(bfs):
+    rp, col = G.path_graph(5)
+    g = bfs.bfs_graph_upload(rp, col)
+    d = torch.empty(5, dtype=torch.int32, device="cuda")
+    for src in (-1, 5):
+        with pytest.raises(bfs.BfsError) as e:
+            bfs.bfs_single(g, src, d)
+        assert e.value.code == bfs.BFS_EINVAL
+    with pytest.raises(bfs.BfsError):
+        bfs.bfs_single_ex(g, 0, d, params=bfs.make_params(chunk=10))
+    g.free()
+    bad = col.copy()
+    bad[0] = 9
+    with pytest.raises(bfs.BfsError) as e:
+        bfs.bfs_graph_upload(rp, bad, flags=bfs.BFS_VALIDATE)
+    assert e.value.code == bfs.BFS_EINVAL
+    rp2, col2 = G.csr_from_edges(4, [(0, 1), (1, 2)], symmetric=False)
+    with pytest.raises(bfs.BfsError):
+        bfs.bfs_graph_upload(rp2, col2, flags=bfs.BFS_VALIDATE_SYMMETRY)
+    rp3 = rp.copy()
+    rp3[2], rp3[3] = rp3[3], rp3[2]
+    with pytest.raises(bfs.BfsError):
+        bfs.bfs_graph_upload(rp3, col, flags=bfs.BFS_VALIDATE)
+
+
+def test_barrier_timeout_reports_status(bfs):
+    """The grid barrier waits for one block more than launched: the bounded wait
+    runs out, the query returns BFS_ETIMEOUT, and the context stays usable."""
+    rp, col = G.path_graph(64)
+    g = bfs.bfs_graph_upload(rp, col)
+    d = torch.empty(64, dtype=torch.int32, device="cuda")
+    with pytest.raises(bfs.BfsError) as e:
+        bfs.bfs_single_ex(g, 0, d, params=bfs.make_params(test_barrier_extra=1, timeout_ms=50))
+    assert e.value.code == bfs.BFS_ETIMEOUT
+    bfs.bfs_single(g, 3, d)
+    assert np.array_equal(d.cpu().numpy(), oracle.bfs(rp, col, 3))
+    g.free()
+
+
+def test_graph_info(bfs):
+    rp, col = G.csr_from_edges(10, [(0, 1), (0, 2), (0, 3)])
+    g = bfs.bfs_graph_upload(rp, col)
+    assert g.info() == {"n": 10, "m": 6, "max_degree": 3, "isolated": 6}
+    g.free()
