@@ -46,6 +46,13 @@ inline uint64_t rand64(uint64_t seed, uint64_t stream, uint64_t idx) {
   return mix64(key + (idx + 1) * kGolden);
 }
 
+// The same draws as rand64 with the per-(seed, stream) key computed once.
+struct StreamGen {
+  uint64_t key;
+  StreamGen(uint64_t seed, uint64_t stream) : key(mix64(seed ^ mix64(stream + kGolden))) {}
+  uint64_t operator()(uint64_t idx) const { return mix64(key + (idx + 1) * kGolden); }
+};
+
 // Uniform double in [0, 1) from the top 53 bits.
 inline double u01(uint64_t r) { return (double)(r >> 11) * (1.0 / 9007199254740992.0); }
 
@@ -69,10 +76,13 @@ enum : uint64_t {
 
 struct gg_csr {
   int64_t n = 0;
-  // Rows after sort+unique live in tmp[off[v] .. off[v] + deg[v]).
+  // Rows after sort+unique live in tmp[off[v] .. off[v] + deg[v]), or, when
+  // `packed`, in the low 32 bits of arcs[off[v] .. off[v] + deg[v]).
   std::vector<int64_t> off;
   std::vector<int64_t> deg;
   std::vector<int32_t> tmp;
+  std::vector<uint64_t> arcs;
+  bool packed = false;
   int64_t m = 0;  // sum of deg
 };
 
@@ -113,10 +123,90 @@ void sort_unique_rows(gg_csr* g) {
   g->m = total;
 }
 
+// Parallel build: arcs (u,v) and (v,u) of every pair are radix-partitioned by
+// the high bits of their first vertex into thread-private runs, then every
+// bucket is sorted and de-duplicated on its own.  Same CSR as the serial path.
+gg_csr* build_bucketed(int64_t n, int64_t npairs, const uint32_t* pu, const uint32_t* pv) {
+  int bits = 0;
+  while (((int64_t)1 << bits) < n) ++bits;
+  const int bbits = bits > 12 ? 12 : bits;
+  const int shift = bits - bbits;
+  const int64_t nb = (int64_t)1 << bbits;
+  const int T = num_threads();
+  std::vector<int64_t> hist((size_t)T * (size_t)nb, 0);
+  gg_csr* g = new gg_csr();
+  g->n = n;
+  g->packed = true;
+#pragma omp parallel num_threads(T)
+  {
+#ifdef _OPENMP
+    const int t = omp_get_thread_num();
+#else
+    const int t = 0;
+#endif
+    const int64_t lo = npairs * t / T, hi = npairs * (t + 1) / T;
+    int64_t* h = hist.data() + (size_t)t * (size_t)nb;
+    for (int64_t k = lo; k < hi; ++k) {
+      if (pu[k] == pv[k]) continue;
+      h[pu[k] >> shift]++;
+      h[pv[k] >> shift]++;
+    }
+  }
+  std::vector<int64_t> bstart(nb + 1, 0);
+  int64_t acc = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    bstart[b] = acc;
+    for (int t = 0; t < T; ++t) {
+      int64_t c = hist[(size_t)t * (size_t)nb + b];
+      hist[(size_t)t * (size_t)nb + b] = acc;
+      acc += c;
+    }
+  }
+  bstart[nb] = acc;
+  g->arcs.resize((size_t)acc);
+  uint64_t* arcs = g->arcs.data();
+#pragma omp parallel num_threads(T)
+  {
+#ifdef _OPENMP
+    const int t = omp_get_thread_num();
+#else
+    const int t = 0;
+#endif
+    const int64_t lo = npairs * t / T, hi = npairs * (t + 1) / T;
+    int64_t* h = hist.data() + (size_t)t * (size_t)nb;
+    for (int64_t k = lo; k < hi; ++k) {
+      const uint64_t a = pu[k], b = pv[k];
+      if (a == b) continue;
+      arcs[h[a >> shift]++] = (a << 32) | b;
+      arcs[h[b >> shift]++] = (b << 32) | a;
+    }
+  }
+  g->off.assign(n + 1, 0);
+  g->deg.assign(n, 0);
+  int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
+  for (int64_t b = 0; b < nb; ++b) {
+    uint64_t* s0 = arcs + bstart[b];
+    uint64_t* e0 = arcs + bstart[b + 1];
+    std::sort(s0, e0);
+    uint64_t* e1 = std::unique(s0, e0);
+    const int64_t base = bstart[b];
+    for (uint64_t* p = s0; p < e1; ++p) {
+      const int64_t u = (int64_t)(*p >> 32);
+      if (g->deg[u] == 0) g->off[u] = base + (p - s0);
+      g->deg[u]++;
+    }
+    total += e1 - s0;
+  }
+  g->m = total;
+  return g;
+}
+
 // Build a symmetric CSR from a list of undirected pairs (u[k], v[k]); self
 // loops are dropped, duplicates removed, rows sorted.
 gg_csr* build_from_pairs(int64_t n, int64_t npairs, const uint32_t* pu, const uint32_t* pv,
                          bool serial) {
+  if (!serial && npairs >= ((int64_t)1 << 20)) return build_bucketed(n, npairs, pu, pv);
   gg_csr* g = new gg_csr();
   g->n = n;
   std::vector<int64_t> cnt(n, 0);
@@ -206,9 +296,18 @@ void copy_out(const gg_csr* g, int64_t* row_ptr, int32_t* col) {
   const int64_t n = g->n;
   std::vector<int64_t> rp(n + 1);
   exclusive_scan(g->deg.data(), n, rp.data());
+  if (g->packed) {
 #pragma omp parallel for schedule(dynamic, 4096)
-  for (int64_t v = 0; v < n; ++v) {
-    std::memcpy(col + rp[v], g->tmp.data() + g->off[v], sizeof(int32_t) * (size_t)g->deg[v]);
+    for (int64_t v = 0; v < n; ++v) {
+      const uint64_t* a = g->arcs.data() + g->off[v];
+      int32_t* c = col + rp[v];
+      for (int64_t i = 0; i < g->deg[v]; ++i) c[i] = (int32_t)(uint32_t)(a[i] & 0xffffffffull);
+    }
+  } else {
+#pragma omp parallel for schedule(dynamic, 4096)
+    for (int64_t v = 0; v < n; ++v) {
+      std::memcpy(col + rp[v], g->tmp.data() + g->off[v], sizeof(int32_t) * (size_t)g->deg[v]);
+    }
   }
   std::memcpy(row_ptr, rp.data(), sizeof(int64_t) * (size_t)(n + 1));
 }
@@ -234,21 +333,18 @@ gg_csr* gg_rmat(int scale, int edgefactor, double a, double b, double c, uint64_
   const double ab = a + b, abc = a + b + c;
   std::vector<uint32_t> perm = fisher_yates(n, perm_seed);
   std::vector<uint32_t> pu(npairs), pv(npairs);
+  // u01(r) < t  <=>  (r >> 11) < ceil(t * 2^53): the same comparisons in integers.
+  const double two53 = 9007199254740992.0;
+  const uint64_t t1 = (uint64_t)std::ceil(a * two53), t2 = (uint64_t)std::ceil(ab * two53),
+                 t3 = (uint64_t)std::ceil(abc * two53);
+  const StreamGen rng(seed, kStreamRmat);
 #pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < npairs; ++k) {
     uint64_t row = 0, col = 0;
+    const uint64_t base = (uint64_t)k * (uint64_t)scale;
     for (int lvl = 0; lvl < scale; ++lvl) {
-      double u = u01(rand64(seed, kStreamRmat, (uint64_t)k * (uint64_t)scale + (uint64_t)lvl));
-      uint64_t rb, cb;
-      if (u < a) {
-        rb = 0; cb = 0;
-      } else if (u < ab) {
-        rb = 0; cb = 1;
-      } else if (u < abc) {
-        rb = 1; cb = 0;
-      } else {
-        rb = 1; cb = 1;
-      }
+      const uint64_t x = rng(base + (uint64_t)lvl) >> 11;
+      const uint64_t rb = x >= t2, cb = (x >= t1) & ((x < t2) | (x >= t3));
       row = (row << 1) | rb;
       col = (col << 1) | cb;
     }
