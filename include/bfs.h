@@ -184,6 +184,38 @@ int bfs_single(bfs_graph *g, int32_t src, int32_t *dist, void *stream);
 int bfs_single_ex(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *params,
                   bfs_stats *stats, bfs_level_stat *levels, int32_t level_cap, void *stream);
 
+/*
+ * bfs_single distances without any memory allocation (the paper has no
+ * counterpart; this is a library-usage variant).
+ *
+ * For callers that cannot allocate device memory when they run a query: code
+ * confined to a memory pool or arena it does not own, contexts where an
+ * allocation could block on the allocator or synchronize the device, or
+ * processes that reserved all device memory in advance.  The caller passes
+ * the graph and the output as device pointers; the kernel's scratch (bitmaps,
+ * frontier queues, control block) lives in one static device array of
+ * 64 MiB that the library reserves on every GPU where it is loaded, until the
+ * process exits.  Nothing is allocated by this call: no cudaMalloc, no
+ * cudaFree, no allocating library routine.
+ *  row_ptr, row_ptr_bits, col_idx, n, m   the CSR graph as in
+ *        bfs_graph_upload, but already in DEVICE memory and not copied or
+ *        validated (it must be a valid symmetric CSR).
+ *  src   source vertex in [0, n).
+ *  dist  device int32[n] output (-1 = unreachable).
+ * Limit: the scratch needs about 24.5*n + m/16 bytes (each of its nine regions
+ * rounded up to 256 bytes); larger graphs get BFS_ENOMEM.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents: calls
+ * that may overlap on the GPU (other streams, unordered host threads) race
+ * with each other and must be serialized by the caller.
+ * Uses the default parameters (policy AUTO).  Blocks until the query has
+ * finished.  Errors: BFS_EINVAL, BFS_ENOMEM (too large), BFS_ECUDA,
+ * BFS_ETIMEOUT.
+ */
+int bfs_single_noalloc(const void *row_ptr, int row_ptr_bits, const int32_t *col_idx, int64_t n,
+                       int64_t m, int32_t src, int32_t *dist, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,6 +102,7 @@ _SIGNATURES = [
     ("bfs_single", ctypes.c_int, [_vp, _i32, _vp, _vp]),
     ("bfs_single_ex", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_stats),
                                      _vp, _i32, _vp]),
+    ("bfs_single_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _i64, _i32, _vp, _vp]),
 ]
 
 
@@ -253,3 +254,15 @@ def bfs_single_ex(g: Graph, src: int, dist, params: bfs_params | None = None, st
     _check(rc, "bfs_single_ex")
     levels = [lv[i].as_dict() for i in range(min(st.levels, level_cap))] if lv is not None else []
     return (st.as_dict() if st is not None else None), levels
+
+
+def bfs_single_noalloc(row_ptr, col_idx, src: int, dist, stream=None):
+    """Distances from ``src`` with no allocation: ``row_ptr`` (int32/int64),
+    ``col_idx`` (int32) and ``dist`` (int32[n]) are torch CUDA tensors; the
+    scratch is the library's static 64 MiB device array (see include/bfs.h)."""
+    bits = row_ptr.element_size() * 8
+    n = row_ptr.numel() - 1
+    m = col_idx.numel()
+    _check(load().bfs_single_noalloc(_ptr(row_ptr), bits, _ptr(col_idx) if m else None, n, m, int(src), _ptr(dist),
+                                     _stream_handle(stream)), "bfs_single_noalloc")
+    return dist

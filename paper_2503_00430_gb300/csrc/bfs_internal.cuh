@@ -140,5 +140,7 @@ int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
                bfs_level_stat* levels, int level_cap, cudaStream_t stream);
+int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads_per_block,
+                               cudaStream_t stream);
 
 }  // namespace gbfs

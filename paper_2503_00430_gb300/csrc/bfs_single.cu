@@ -827,6 +827,21 @@ static int launch_graph(bfs_graph* g, KParams& K, const bfs_params& p, cudaStrea
   return BFS_OK;
 }
 
+// Launch the persistent kernel (no statistics) on prepared arguments, with the
+// default block shape: used by the entry point whose scratch lives in a static
+// device array and that therefore has no bfs_graph object.
+int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads_per_block,
+                               cudaStream_t stream) {
+  void* fn = rp_bits == 32 ? Kernels<int, false>::persistent() : Kernels<long long, false>::persistent();
+  int per_sm = 0;
+  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads_per_block, 0));
+  if (per_sm < 1) return BFS_EINVAL;
+  dim3 grid((unsigned)(per_sm * num_sms)), block((unsigned)threads_per_block);
+  void* args[] = {&K};
+  GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, 0, stream));
+  return BFS_OK;
+}
+
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
                bfs_level_stat* levels, int level_cap, cudaStream_t stream) {
   SingleWs& ws = g->ws;
