@@ -87,16 +87,19 @@ typedef struct bfs_params {
     int32_t small_max;       /* top-down: vertices with degree < small_max (<= 32) are expanded
                                 32 at a time by one warp; larger ones get a warp each (default 32) */
     int32_t chunk;           /* top-down: a vertex's adjacency is split into work items of at most
-                                `chunk` edges (256..65535, default 4096) */
-    int32_t bu_warp_min;     /* bottom-up: an unvisited vertex with degree > bu_warp_min is scanned by
-                                the whole warp instead of one lane (default 32) */
+                                `chunk` edges (256..65535, default 1024) */
+    int32_t bu_warp_min;     /* bottom-up: an unvisited vertex with degree > bu_warp_min (<= 2^24) is
+                                scanned on its own by the whole warp; smaller ones share the warp's
+                                32-entry steps with their neighbours in the bitmap word (default 32) */
     int32_t threads_per_block; /* 128..1024, multiple of 32 (default 512) */
     int32_t blocks_per_sm;   /* 0 = as many as fit (cooperative launch limit) */
     int32_t timeout_ms;      /* limit of every device-side barrier wait (default 10000) */
     uint64_t script;         /* BFS_POLICY_SCRIPT direction bits */
     int32_t test_barrier_extra; /* testing only: grid barriers wait for this many blocks more than
                                    were launched, so a wait runs out and BFS_ETIMEOUT is returned */
-    int32_t reserved[9];
+    int32_t bu_chunk;        /* bottom-up: groups of 32 bitmap words a warp takes per grab from a shared
+                                cursor (0 = static interleaved assignment; default 1) */
+    int32_t reserved[8];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique
@@ -126,6 +129,8 @@ typedef struct bfs_level_stat {
     int64_t edges;           /* top-down: degrees in F_L; bottom-up: entries examined */
     int64_t unvisited;       /* bottom-up: unvisited vertices of degree > 0 (0 for top-down) */
     int64_t found;           /* |F_{L+1}| */
+    int64_t ns;              /* persistent launch: device time from the end of the previous level
+                                (including any conversion) to the end of this one */
 } bfs_level_stat;
 
 /* Message for a BFS_* code (static string). */

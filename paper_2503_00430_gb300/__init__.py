@@ -60,7 +60,7 @@ class bfs_params(ctypes.Structure):
         ("small_max", ctypes.c_int32), ("chunk", ctypes.c_int32), ("bu_warp_min", ctypes.c_int32),
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("timeout_ms", ctypes.c_int32), ("script", ctypes.c_uint64),
-        ("test_barrier_extra", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9),
+        ("test_barrier_extra", ctypes.c_int32), ("bu_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8),
     ]
 
 
@@ -81,6 +81,7 @@ class bfs_level_stat(ctypes.Structure):
     _fields_ = [
         ("direction", ctypes.c_int32), ("converted", ctypes.c_int32), ("frontier", ctypes.c_int64),
         ("edges", ctypes.c_int64), ("unvisited", ctypes.c_int64), ("found", ctypes.c_int64),
+        ("ns", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -214,9 +214,10 @@ static int check_params(const bfs_params& p) {
   if (p.alpha < 1 || p.beta < 1 || p.tau_inv < 1) return BFS_EINVAL;
   if (p.small_max < 1 || p.small_max > 32) return BFS_EINVAL;
   if (p.chunk < 256 || p.chunk > 65535) return BFS_EINVAL;
-  if (p.bu_warp_min < 0) return BFS_EINVAL;
+  if (p.bu_warp_min < 0 || p.bu_warp_min > (1 << 24)) return BFS_EINVAL;
   if (p.threads_per_block < 64 || p.threads_per_block > 1024 || (p.threads_per_block & 31)) return BFS_EINVAL;
   if (p.blocks_per_sm < 0 || p.timeout_ms < 1 || p.test_barrier_extra < 0) return BFS_EINVAL;
+  if (p.bu_chunk < 0 || p.bu_chunk > 65536) return BFS_EINVAL;
   return BFS_OK;
 }
 
@@ -252,13 +253,14 @@ void bfs_params_default(bfs_params* p) {
   p->tau_inv = 20;
   p->large_diameter_degree = 7;
   p->small_max = 32;
-  p->chunk = 4096;
+  p->chunk = 1024;
   p->bu_warp_min = 32;
   p->threads_per_block = 512;
   p->blocks_per_sm = 0;
   p->timeout_ms = 10000;
   p->script = 0;
   p->test_barrier_extra = 0;
+  p->bu_chunk = 1;
 }
 
 int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n, int64_t m,

@@ -18,6 +18,7 @@ struct Slot {
   unsigned long long nv;     // |F_L|
   unsigned long long mf;     // sum of degrees over F_L
   unsigned long long nq;     // vertex-queue entries written by a bitmap -> queue conversion
+  unsigned long long cursor; // bottom-up: next bitmap word to hand out (dynamic assignment)
 };
 
 // Device control block of one single-source query (zeroed before each launch).
@@ -53,7 +54,7 @@ struct KParams {
   int lst_cap;
   int policy, alpha, beta, tau_inv;
   unsigned long long script;
-  int small_max, chunk, bu_warp_min;
+  int small_max, chunk, bu_warp_min, bu_chunk;
   int need_qv;
   long long timeout_ns;
   int barrier_extra;

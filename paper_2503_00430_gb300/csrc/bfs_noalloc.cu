@@ -149,6 +149,7 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   K.small_max = p.small_max;
   K.chunk = p.chunk;
   K.bu_warp_min = p.bu_warp_min;
+  K.bu_chunk = p.bu_chunk;
   K.need_qv = K.policy != BFS_POLICY_TD_ONLY;
   K.timeout_ns = (long long)p.timeout_ms * 1000000ll;
   K.barrier_extra = 0;

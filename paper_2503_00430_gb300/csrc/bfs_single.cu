@@ -236,54 +236,110 @@ __device__ void seed_phase(const KParams& P) {
 
 // ---------------------------------------------------------------- top-down
 
-// Warp-collective: visit neighbour u (u < 0: none) at level L.  A clear
-// visited bit is claimed with atomicOr; the claiming lane stores dist and the
-// warp appends the new vertices (vertex queue and degree-binned work items).
+// Warp-collective: visit up to four neighbours per lane (c[k] < 0: none) at
+// level L.  All four visited words are read before any is claimed, all claims
+// (atomicOr on the bitmap word) are issued before any result is used, and the
+// degrees of the claimed vertices are fetched together, so one lane keeps
+// several memory requests in flight.  The lane that set a bit is the only
+// writer of that vertex's dist (a plain store) and appends it to the next
+// frontier: vertex queue and degree-binned work items, one set of atomics per
+// warp.
 template <typename RP>
-__device__ __forceinline__ void td_visit(const KParams& P, int L, int u, Slot* out, int* qvn,
-                                         unsigned long long* itn) {
-  bool claimed = false;
-  if (u >= 0) {
-    unsigned* wp = P.vis + (u >> 5);
-    const unsigned bit = 1u << (u & 31);
-    if (!(ld_relaxed_u32(wp) & bit)) claimed = !(atomicOr(wp, bit) & bit);
+__device__ __forceinline__ void td_visit4(const KParams& P, int L, const int (&c)[4], Slot* out, int* qvn,
+                                          unsigned long long* itn) {
+  unsigned cur[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) cur[k] = c[k] >= 0 ? ld_relaxed_u32(P.vis + (c[k] >> 5)) : kFull;
+  unsigned old[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned bit = 1u << (c[k] & 31);
+    old[k] = (c[k] >= 0 && !(cur[k] & bit)) ? atomicOr(P.vis + (c[k] >> 5), bit) : kFull;
   }
-  const unsigned mask = __ballot_sync(kFull, claimed);
-  if (mask == 0) return;
-  long long s = 0;
-  int d = 0;
-  if (claimed) {
-    P.dist[u] = L + 1;  // single writer: the lane that set the bit
-    s = rp_at<RP>(P.rp, u);
-    d = (int)(rp_at<RP>(P.rp, (long long)u + 1) - s);
-  }
-  const unsigned lane = lane_id();
-  const int nsm = (claimed && d > 0 && d < P.small_max) ? 1 : 0;
-  const int nlg = (claimed && d >= P.small_max) ? (d + P.chunk - 1) / P.chunk : 0;
-  const unsigned smask = __ballot_sync(kFull, nsm);
-  const int lg_incl = warp_incl_scan(nlg);
-  const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
-  const unsigned long long dsum = warp_sum_u64((unsigned long long)d);
-  const int leader = __ffs(mask) - 1;
-  unsigned long long b_items = 0, b_q = 0;
-  if ((int)lane == leader) {
-    b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
-    b_q = atomicAdd(&out->nv, (unsigned long long)__popc(mask));
-    atomicAdd(&out->mf, dsum);
-  }
-  b_items = __shfl_sync(kFull, b_items, leader);
-  b_q = __shfl_sync(kFull, b_q, leader);
-  const unsigned lt = lanemask_lt();
-  if (claimed && P.need_qv) qvn[b_q + __popc(mask & lt)] = u;
-  if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
-  if (nlg) {
-    unsigned long long b = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
-    for (int c = 0; c < nlg; ++c) {
-      int len = d - c * P.chunk;
-      if (len > P.chunk) len = P.chunk;
-      itn[P.cap - 1 - (long long)(b + c)] = pack_item(s + (long long)c * P.chunk, len);
+  unsigned cl = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (!(old[k] & (1u << (c[k] & 31)))) cl |= 1u << k;
+  if (__ballot_sync(kFull, cl != 0) == 0) return;
+  long long s[4];
+  int d[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    s[k] = 0;
+    d[k] = 0;
+    if ((cl >> k) & 1u) {
+      P.dist[c[k]] = L + 1;
+      s[k] = rp_at<RP>(P.rp, c[k]);
+      d[k] = (int)(rp_at<RP>(P.rp, (long long)c[k] + 1) - s[k]);
     }
   }
+  const int ncl = __popc(cl);
+  int nsm = 0, nlg = 0;
+  unsigned long long dsum = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if ((cl >> k) & 1u) {
+      if (d[k] > 0 && d[k] < P.small_max) ++nsm;
+      else if (d[k] >= P.small_max) nlg += (d[k] + P.chunk - 1) / P.chunk;
+      dsum += (unsigned long long)d[k];
+    }
+  }
+  const int q_incl = warp_incl_scan(ncl), sm_incl = warp_incl_scan(nsm), lg_incl = warp_incl_scan(nlg);
+  const int q_tot = __shfl_sync(kFull, q_incl, 31), sm_tot = __shfl_sync(kFull, sm_incl, 31),
+            lg_tot = __shfl_sync(kFull, lg_incl, 31);
+  const unsigned long long dsum_tot = warp_sum_u64(dsum);
+  unsigned long long b_items = 0, b_q = 0;
+  if (lane_id() == 0) {
+    b_items = atomicAdd(&out->items, (unsigned long long)sm_tot | ((unsigned long long)lg_tot << 32));
+    b_q = atomicAdd(&out->nv, (unsigned long long)q_tot);
+    atomicAdd(&out->mf, dsum_tot);
+  }
+  b_items = __shfl_sync(kFull, b_items, 0);
+  b_q = __shfl_sync(kFull, b_q, 0);
+  unsigned long long qi = b_q + (unsigned long long)(q_incl - ncl);
+  unsigned long long si = (b_items & 0xffffffffull) + (unsigned long long)(sm_incl - nsm);
+  unsigned long long li = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!((cl >> k) & 1u)) continue;
+    if (P.need_qv) qvn[qi++] = c[k];
+    if (d[k] > 0 && d[k] < P.small_max) {
+      itn[si++] = pack_item(s[k], d[k]);
+    } else if (d[k] >= P.small_max) {
+      for (int o = 0; o < d[k]; o += P.chunk) {
+        const int len = d[k] - o < P.chunk ? d[k] - o : P.chunk;
+        itn[P.cap - 1 - (long long)(li++)] = pack_item(s[k] + o, len);
+      }
+    }
+  }
+}
+
+// Position of the n-th (0-based) set bit of mask, by halving the window with
+// population counts; always in [0, 31].
+__device__ __forceinline__ int nth_set_bit(unsigned mask, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const int c = __popc(mask & ((1u << w) - 1u));
+    if (n >= c) {
+      n -= c;
+      mask >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+// Lane holding entry e of the concatenation described by the exclusive scan
+// `excl` of 32 lengths (largest lane whose start is <= e).
+__device__ __forceinline__ int owner_of(int excl, int e) {
+  int lo = 0;
+#pragma unroll
+  for (int step = 16; step >= 1; step >>= 1) {
+    const int ex = __shfl_sync(kFull, excl, lo + step);
+    if (ex <= e) lo += step;
+  }
+  return lo;
 }
 
 template <typename RP, bool STATS>
@@ -294,10 +350,12 @@ __device__ void td_phase(const KParams& P, int L, unsigned long long items_cur) 
   int* qvn = (L & 1) ? P.qv0 : P.qv1;
   Slot* out = &P.ctrl->slot[(L + 1) & 3];
   const unsigned lane = lane_id();
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // Block-major warp order: consecutive work goes to different blocks (SMs).
+  const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   Acc acc;
-  // Small items: 32 per warp, edges dealt to lanes by an exclusive scan of lengths.
+  // Small items: 32 per warp; their edges are dealt to the lanes through an
+  // exclusive scan of the lengths, 128 per step (four per lane).
   for (long long g = gw; (unsigned long long)g * 32ull < nsmall; g += nwarps) {
     const unsigned long long i = (unsigned long long)g * 32ull + lane;
     const unsigned long long item = i < nsmall ? it[i] : 0ull;
@@ -307,22 +365,20 @@ __device__ void td_phase(const KParams& P, int L, unsigned long long items_cur) 
     const int excl = incl - len;
     const int total = __shfl_sync(kFull, incl, 31);
     if (STATS) acc.edges += (unsigned long long)len;
-    for (int base = 0; base < total; base += 32) {
-      const int e = base + (int)lane;
-      int lo = 0;
+    for (int base = 0; base < total; base += 128) {
+      int c[4];
 #pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        const int ex = __shfl_sync(kFull, excl, lo + step);
-        if (ex <= e) lo += step;
+      for (int k = 0; k < 4; ++k) {
+        const int e = base + 32 * k + (int)lane;
+        const int o = owner_of(excl, e);
+        const long long so = __shfl_sync(kFull, s, o);
+        const int exo = __shfl_sync(kFull, excl, o);
+        c[k] = e < total ? __ldg(P.col + so + (e - exo)) : -1;
       }
-      const long long so = __shfl_sync(kFull, s, lo);
-      const int exo = __shfl_sync(kFull, excl, lo);
-      int u = -1;
-      if (e < total) u = __ldg(P.col + so + (e - exo));
-      td_visit<RP>(P, L, u, out, qvn, itn);
+      td_visit4<RP>(P, L, c, out, qvn, itn);
     }
   }
-  // Large items: one warp per item, 128-bit loads of the aligned span.
+  // Large items (<= chunk edges each): one warp per item, 128-bit loads of the aligned span.
   for (long long i = gw; (unsigned long long)i < nlarge; i += nwarps) {
     const unsigned long long item = it[P.cap - 1 - i];
     const long long s = (long long)(item >> 16);
@@ -333,14 +389,9 @@ __device__ void td_phase(const KParams& P, int L, unsigned long long items_cur) 
       const long long j = base + 4 * (long long)lane;
       int4 q = make_int4(-1, -1, -1, -1);
       if (j < e) q = __ldg(reinterpret_cast<const int4*>(P.col + j));
-      const int c0 = (j >= s && j < e) ? q.x : -1;
-      const int c1 = (j + 1 >= s && j + 1 < e) ? q.y : -1;
-      const int c2 = (j + 2 >= s && j + 2 < e) ? q.z : -1;
-      const int c3 = (j + 3 >= s && j + 3 < e) ? q.w : -1;
-      td_visit<RP>(P, L, c0, out, qvn, itn);
-      td_visit<RP>(P, L, c1, out, qvn, itn);
-      td_visit<RP>(P, L, c2, out, qvn, itn);
-      td_visit<RP>(P, L, c3, out, qvn, itn);
+      const int c[4] = {(j >= s && j < e) ? q.x : -1, (j + 1 >= s && j + 1 < e) ? q.y : -1,
+                        (j + 2 >= s && j + 2 < e) ? q.z : -1, (j + 3 >= s && j + 3 < e) ? q.w : -1};
+      td_visit4<RP>(P, L, c, out, qvn, itn);
     }
   }
   if (STATS) flush_acc<STATS>(P, L, acc, out, false);
@@ -352,60 +403,106 @@ __device__ __forceinline__ bool in_frontier(const unsigned* front, int u) {
   return (front[u >> 5] >> (u & 31)) & 1u;
 }
 
-template <typename RP, bool STATS>
-__device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigned* next) {
-  Slot* out = &P.ctrl->slot[(L + 1) & 3];
+// Shared-memory staging of one warp in a bottom-up batch.
+constexpr int kPendCap = 64;  // deferred long scans per warp (two rounds of 32 lanes)
+struct BuWarpSmem {
+  unsigned next[32];             // new-frontier bits of the batch's 32 words
+  long long pstart[kPendCap];    // deferred scan: next entry to examine
+  int plen[kPendCap];            // entries left
+  int pv[kPendCap];              // vertex
+  int pd[kPendCap];              // its degree
+  int pex[kPendCap];             // entries examined so far (statistics)
+  int npend;
+};
+
+__device__ __forceinline__ void bu_mark_found(const KParams& P, int L, BuWarpSmem& sm, long long w0, int v, int d,
+                                              Acc& acc) {
+  atomicOr(&sm.next[(int)((long long)v / 32 - w0)], 1u << (v & 31));
+  P.dist[v] = L + 1;
+  acc.found += 1;
+  acc.mf += (unsigned long long)d;
+}
+
+// Warp-collective: finish this warp's deferred scans.  The remaining
+// adjacency ranges are scanned as one concatenation, four entries per lane per
+// step (four column loads, then four frontier probes, in flight together); a
+// vertex's remaining entries are skipped once it has found a parent.  Ranges
+// longer than bu_warp_min are scanned one at a time by the whole warp.
+template <bool STATS>
+__device__ void bu_drain(const KParams& P, int L, const unsigned* front, BuWarpSmem& sm, long long w0, Acc& acc) {
   const unsigned lane = lane_id();
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  Acc acc;
-  for (long long w = gw; w < P.nw; w += nwarps) {
-    const unsigned vis = P.vis[w];
-    if (vis == kFull) {
-      if (lane == 0) next[w] = 0u;
-      continue;
-    }
-    const long long v = w * 32 + lane;
-    const bool active = !((vis >> lane) & 1u);  // padding bits past n are set, so v < n here
-    long long s = 0, e = 0;
-    if (active) {
-      s = rp_at<RP>(P.rp, v);
-      e = rp_at<RP>(P.rp, v + 1);
-    }
-    const long long d = e - s;
-    bool found = false;
-    long long examined = 0;
-    const bool heavy = active && d > P.bu_warp_min;
-    if (active && !heavy) {
-      long long j = s, hit = -1;
-      for (; j < e && (j & 3); ++j) {
-        if (in_frontier(front, __ldg(P.col + j))) {
-          hit = j;
-          break;
+  __syncwarp();
+  const int np = sm.npend;
+  for (int g0 = 0; g0 < np; g0 += 32) {
+    const int j = g0 + (int)lane;
+    const bool have = j < np;
+    const long long ps = have ? sm.pstart[j] : 0;
+    const int pl = have ? sm.plen[j] : 0;
+    const int pv = have ? sm.pv[j] : 0;
+    const int pdeg = have ? sm.pd[j] : 0;
+    int ex = have ? sm.pex[j] : 0;
+    const bool heavy = pl > P.bu_warp_min;
+    const int len = heavy ? 0 : pl;
+    const int incl = warp_incl_scan(len);
+    const int excl = incl - len;
+    const int total = __shfl_sync(kFull, incl, 31);
+    unsigned pend = __ballot_sync(kFull, len > 0);
+    unsigned fnd = 0;
+    int last = (int)__reduce_max_sync(kFull, (unsigned)(((pend >> lane) & 1u) ? incl : 0));
+    for (int base = 0; base < last; base += 128) {
+      int o[4], u[4];
+      bool want[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ei = base + 32 * k + (int)lane;
+        o[k] = owner_of(excl, ei);
+        const long long so = __shfl_sync(kFull, ps, o[k]);
+        const int exo = __shfl_sync(kFull, excl, o[k]);
+        want[k] = ei < total && ((pend >> o[k]) & 1u);
+        u[k] = want[k] ? __ldg(P.col + so + (ei - exo)) : 0;
+      }
+      bool hk[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const unsigned fw = want[k] ? front[u[k] >> 5] : 0u;
+        hk[k] = (fw >> (u[k] & 31)) & 1u;
+      }
+      unsigned mine = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (hk[k]) mine |= 1u << o[k];
+      const unsigned hm = __reduce_or_sync(kFull, mine) & pend;
+      if (STATS && hm) {
+        unsigned t = hm;
+        while (t) {
+          const int oo = __ffs(t) - 1;
+          t &= t - 1;
+          unsigned best = 0xffffffffu;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (hk[k] && o[k] == oo) best = min(best, (unsigned)(base + 32 * k + (int)lane));
+          const unsigned mn = __reduce_min_sync(kFull, best);
+          if ((int)lane == oo) ex += (int)mn - excl + 1;
         }
       }
-      if (hit < 0) {
-        for (; j < e; j += 4) {
-          const int4 q = __ldg(reinterpret_cast<const int4*>(P.col + j));
-          if (in_frontier(front, q.x)) { hit = j; break; }
-          if (j + 1 < e && in_frontier(front, q.y)) { hit = j + 1; break; }
-          if (j + 2 < e && in_frontier(front, q.z)) { hit = j + 2; break; }
-          if (j + 3 < e && in_frontier(front, q.w)) { hit = j + 3; break; }
-        }
-      }
-      found = hit >= 0;
-      examined = found ? hit - s + 1 : d;
+      pend &= ~hm;
+      fnd |= hm;
+      if (!pend) break;
+      last = (int)__reduce_max_sync(kFull, (unsigned)(((pend >> lane) & 1u) ? incl : 0));
     }
+    bool found = (fnd >> lane) & 1u;
+    if (STATS && len > 0 && !found) ex += len;
     unsigned hv = __ballot_sync(kFull, heavy);
     while (hv) {
       const int h = __ffs(hv) - 1;
       hv &= hv - 1;
-      const long long hs = __shfl_sync(kFull, s, h), he = __shfl_sync(kFull, e, h);
+      const long long hs = __shfl_sync(kFull, ps, h);
+      const long long he = hs + __shfl_sync(kFull, pl, h);
       bool hf = false;
       long long hx = he - hs;
       for (long long b = hs; b < he; b += 32) {
-        const long long j = b + lane;
-        const bool hit = j < he && in_frontier(front, __ldg(P.col + j));
+        const long long jj = b + lane;
+        const bool hit = jj < he && in_frontier(front, __ldg(P.col + jj));
         const unsigned bm = __ballot_sync(kFull, hit);
         if (bm) {
           hf = true;
@@ -415,22 +512,142 @@ __device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigne
       }
       if ((int)lane == h) {
         found = hf;
-        examined = hx;
+        ex += (int)hx;
       }
     }
-    const unsigned fm = __ballot_sync(kFull, found);
-    if (lane == 0) {
-      next[w] = fm;
-      if (fm) P.vis[w] = vis | fm;  // the owning warp is the only writer of this word
-      acc.found += (unsigned long long)__popc(fm);
+    if (found) bu_mark_found(P, L, sm, w0, pv, pdeg, acc);
+    if (STATS && have) acc.edges += (unsigned long long)ex;
+  }
+  __syncwarp();
+  if (lane == 0) sm.npend = 0;
+  __syncwarp();
+}
+
+// One batch of 32 bitmap words (1024 vertices) of a bottom-up level, by one
+// warp.  The unvisited vertices of the batch are packed onto the lanes, two
+// per lane at a time; each looks for a frontier neighbour among the first
+// (aligned) four entries of its adjacency - one 128-bit load and four probes,
+// issued for both vertices before any result is used - and, if it has more
+// entries, is queued for bu_drain.  New-frontier bits are gathered in shared
+// memory and stored once per word, together with the updated visited word.
+template <typename RP, bool STATS>
+__device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigned* next, long long w0,
+                         BuWarpSmem& sm, Acc& acc) {
+  const unsigned lane = lane_id();
+  const long long w = w0 + lane;
+  const unsigned vw = w < P.nw ? P.vis[w] : kFull;
+  const unsigned act = ~vw;  // padding bits past n are set in vis, so act holds vertices < n only
+  sm.next[lane] = 0u;
+  const int cnt = __popc(act);
+  const int incl = warp_incl_scan(cnt);
+  const int excl = incl - cnt;
+  const int total = __shfl_sync(kFull, incl, 31);
+  if (STATS) acc.unvisited += (unsigned long long)cnt;
+  __syncwarp();
+  for (int r0 = 0; r0 < total; r0 += 64) {
+    int v[2];
+    long long s[2], e[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int kk = r0 + 32 * k + (int)lane;
+      const int wo = owner_of(excl, kk);
+      const unsigned aw = __shfl_sync(kFull, act, wo);
+      const int ew = __shfl_sync(kFull, excl, wo);
+      v[k] = -1;
+      if (kk < total) v[k] = (int)((w0 + wo) * 32 + (long long)nth_set_bit(aw, kk - ew));
     }
-    if (found) {
-      P.dist[v] = L + 1;
-      acc.mf += (unsigned long long)d;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      s[k] = 0;
+      e[k] = 0;
+      if (v[k] >= 0) {
+        s[k] = rp_at<RP>(P.rp, v[k]);
+        e[k] = rp_at<RP>(P.rp, (long long)v[k] + 1);
+      }
     }
-    if (STATS) {
-      acc.edges += (unsigned long long)examined;
-      acc.unvisited += active ? 1ull : 0ull;
+    int4 q[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      q[k] = make_int4(0, 0, 0, 0);
+      if (e[k] > s[k]) q[k] = __ldg(reinterpret_cast<const int4*>(P.col + (s[k] & ~3ll)));
+    }
+    unsigned f[2][4];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const long long a0 = s[k] & ~3ll;
+      const int c4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const bool ok = a0 + t >= s[k] && a0 + t < e[k];
+        f[k][t] = ok ? ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u) : 0u;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (v[k] < 0) continue;
+      const long long a0 = s[k] & ~3ll;
+      long long hit = -1;
+#pragma unroll
+      for (int t = 3; t >= 0; --t)
+        if (f[k][t]) hit = a0 + t;
+      const int d = (int)(e[k] - s[k]);
+      const long long rest = a0 + 4;
+      if (hit >= 0) {
+        bu_mark_found(P, L, sm, w0, v[k], d, acc);
+        if (STATS) acc.edges += (unsigned long long)(hit - s[k] + 1);
+      } else if (rest < e[k]) {
+        const int slot = atomicAdd(&sm.npend, 1);
+        sm.pstart[slot] = rest;
+        sm.plen[slot] = (int)(e[k] - rest);
+        sm.pv[slot] = v[k];
+        sm.pd[slot] = d;
+        sm.pex[slot] = (int)(rest - s[k]);
+      } else if (STATS) {
+        acc.edges += (unsigned long long)d;
+      }
+    }
+    __syncwarp();
+    if (sm.npend > kPendCap - 64) bu_drain<STATS>(P, L, front, sm, w0, acc);
+  }
+  if (sm.npend > 0) bu_drain<STATS>(P, L, front, sm, w0, acc);
+  __syncwarp();
+  if (w < P.nw) {
+    const unsigned nx = sm.next[lane];
+    next[w] = nx;
+    if (nx) P.vis[w] = vw | nx;  // this warp is the only writer of its batch's words
+  }
+  __syncwarp();
+}
+
+// Bottom-up level.  Batches of 32 words go to warps statically (interleaved,
+// bu_chunk = 0) or bu_chunk batches at a time from a shared cursor, the next
+// grab being requested before the current one is processed.
+template <typename RP, bool STATS>
+__device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigned* next) {
+  extern __shared__ unsigned long long g_dyn_smem[];  // blockDim.x / 32 BuWarpSmem records
+  BuWarpSmem& sm = reinterpret_cast<BuWarpSmem*>(g_dyn_smem)[threadIdx.x >> 5];
+  Slot* out = &P.ctrl->slot[(L + 1) & 3];
+  const unsigned lane = lane_id();
+  const long long nbatch = ((long long)P.nw + 31) / 32;
+  if (lane == 0) sm.npend = 0;
+  __syncwarp();
+  Acc acc;
+  if (P.bu_chunk <= 0) {
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long b = gw; b < nbatch; b += nwarps) bu_batch<RP, STATS>(P, L, front, next, b * 32, sm, acc);
+  } else {
+    unsigned long long* cur = &P.ctrl->slot[L & 3].cursor;
+    const long long ch = P.bu_chunk;
+    long long b0 = 0;
+    if (lane == 0) b0 = (long long)atomicAdd(cur, (unsigned long long)ch);
+    b0 = __shfl_sync(kFull, b0, 0);
+    while (b0 < nbatch) {
+      long long b1 = 0;
+      if (lane == 0) b1 = (long long)atomicAdd(cur, (unsigned long long)ch);
+      const long long bend = b0 + ch < nbatch ? b0 + ch : nbatch;
+      for (long long b = b0; b < bend; ++b) bu_batch<RP, STATS>(P, L, front, next, b * 32, sm, acc);
+      b0 = __shfl_sync(kFull, b1, 0);
     }
   }
   flush_acc<STATS>(P, L, acc, out, true);
@@ -454,8 +671,47 @@ __device__ void scatter_phase(const int* qv, long long nv, unsigned* bm) {
   }
 }
 
+// Bitmap -> queue for one nonzero word: vertex queue entries and degree-binned
+// work items of the set bits.
+template <typename RP>
+__device__ __forceinline__ void convert_word(const KParams& P, long long w, unsigned word, Slot* out, int* qvn,
+                                             unsigned long long* itn) {
+  const unsigned lane = lane_id();
+  const unsigned lt = lanemask_lt();
+  const bool mine = (word >> lane) & 1u;
+  const long long v = w * 32 + lane;
+  long long s = 0;
+  int d = 0;
+  if (mine) {
+    s = rp_at<RP>(P.rp, v);
+    d = (int)(rp_at<RP>(P.rp, v + 1) - s);
+  }
+  const int nsm = (mine && d > 0 && d < P.small_max) ? 1 : 0;
+  const int nlg = (mine && d >= P.small_max) ? (d + P.chunk - 1) / P.chunk : 0;
+  const unsigned smask = __ballot_sync(kFull, nsm);
+  const int lg_incl = warp_incl_scan(nlg);
+  const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
+  unsigned long long b_items = 0, b_q = 0;
+  if (lane == 0) {
+    b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
+    if (P.need_qv) b_q = atomicAdd(&out->nq, (unsigned long long)__popc(word));
+  }
+  b_items = __shfl_sync(kFull, b_items, 0);
+  b_q = __shfl_sync(kFull, b_q, 0);
+  if (mine && P.need_qv) qvn[b_q + __popc(word & lt)] = (int)v;
+  if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
+  if (nlg) {
+    unsigned long long b = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
+    for (int o = 0; o < d; o += P.chunk) {
+      const int len = d - o < P.chunk ? d - o : P.chunk;
+      itn[P.cap - 1 - (long long)(b++)] = pack_item(s + o, len);
+    }
+  }
+}
+
 // Bitmap -> queue: for the frontier F_{L+1} in bitmap `bm`, write the vertex
-// queue and the degree-binned work items of parity (L+1).
+// queue and the degree-binned work items of parity (L+1).  Words are read 32
+// at a time per warp; only nonzero ones are expanded.
 template <typename RP>
 __device__ void convert_phase(const KParams& P, int L, const unsigned* bm) {
   const int Ln = L + 1;
@@ -465,39 +721,15 @@ __device__ void convert_phase(const KParams& P, int L, const unsigned* bm) {
   const unsigned lane = lane_id();
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned lt = lanemask_lt();
-  for (long long w = gw; w < P.nw; w += nwarps) {
-    const unsigned word = bm[w];
-    if (word == 0u) continue;
-    const bool mine = (word >> lane) & 1u;
-    const long long v = w * 32 + lane;
-    long long s = 0;
-    int d = 0;
-    if (mine) {
-      s = rp_at<RP>(P.rp, v);
-      d = (int)(rp_at<RP>(P.rp, v + 1) - s);
-    }
-    const int nsm = (mine && d > 0 && d < P.small_max) ? 1 : 0;
-    const int nlg = (mine && d >= P.small_max) ? (d + P.chunk - 1) / P.chunk : 0;
-    const unsigned smask = __ballot_sync(kFull, nsm);
-    const int lg_incl = warp_incl_scan(nlg);
-    const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
-    unsigned long long b_items = 0, b_q = 0;
-    if (lane == 0) {
-      b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
-      if (P.need_qv) b_q = atomicAdd(&out->nq, (unsigned long long)__popc(word));
-    }
-    b_items = __shfl_sync(kFull, b_items, 0);
-    b_q = __shfl_sync(kFull, b_q, 0);
-    if (mine && P.need_qv) qvn[b_q + __popc(word & lt)] = (int)v;
-    if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
-    if (nlg) {
-      unsigned long long b = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
-      for (int c = 0; c < nlg; ++c) {
-        int len = d - c * P.chunk;
-        if (len > P.chunk) len = P.chunk;
-        itn[P.cap - 1 - (long long)(b + c)] = pack_item(s + (long long)c * P.chunk, len);
-      }
+  const long long nbatch = ((long long)P.nw + 31) / 32;
+  for (long long b = gw; b < nbatch; b += nwarps) {
+    const long long w = b * 32 + lane;
+    const unsigned word = w < P.nw ? bm[w] : 0u;
+    unsigned todo = __ballot_sync(kFull, word != 0u);
+    while (todo) {
+      const int i = __ffs(todo) - 1;
+      todo &= todo - 1;
+      convert_word<RP>(P, b * 32 + i, __shfl_sync(kFull, word, i), out, qvn, itn);
     }
   }
 }
@@ -514,14 +746,18 @@ struct LoopState {
 };
 
 template <bool STATS>
-__device__ void record_level(const KParams& P, const LoopState& st, long long found, int converted) {
+__device__ void record_level(const KParams& P, const LoopState& st, long long found, int converted,
+                             unsigned long long& t_mark) {
   if (STATS && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long t = globaltimer_ns();
     if (P.lst && st.L < P.lst_cap) {
       P.lst[st.L].direction = st.td ? 0 : 1;
       P.lst[st.L].converted = converted;
       P.lst[st.L].frontier = st.nf_cur;
       P.lst[st.L].found = found;
+      P.lst[st.L].ns = (long long)(t - t_mark);
     }
+    t_mark = t;
     if (st.td) {
       P.ctrl->td_frontier += (unsigned long long)st.nf_cur;
     } else {
@@ -537,6 +773,7 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) seed_phase<RP>(P);
   if (!grid_barrier(P, epoch)) return;
   LoopState st;
+  unsigned long long t_mark = STATS ? globaltimer_ns() : 0ull;
   st.edges_visited = (long long)ld_relaxed_u64(&P.ctrl->slot[0].mf);
   unsigned long long items = ld_relaxed_u64(&P.ctrl->slot[0].items);
   int converted = 0, conversions = 0, tdl = 0, bul = 0;
@@ -544,7 +781,7 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
     const int L = st.L;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       Slot* z = &P.ctrl->slot[(L + 2) & 3];
-      z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0;
+      z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0;
     }
     if (st.td) {
       ++tdl;
@@ -557,7 +794,7 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
     Slot* nx = &P.ctrl->slot[(L + 1) & 3];
     const long long nf = (long long)ld_relaxed_u64(&nx->nv);
     const long long mf = (long long)ld_relaxed_u64(&nx->mf);
-    record_level<STATS>(P, st, nf, converted);
+    record_level<STATS>(P, st, nf, converted, t_mark);
     if (nf == 0) break;
     st.edges_visited += mf;
     st.reached += nf;
@@ -611,7 +848,7 @@ template <typename RP, bool STATS>
 __global__ void __launch_bounds__(1024) k_level(KParams P, int L, int td, int fb, unsigned long long items) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Slot* z = &P.ctrl->slot[(L + 2) & 3];
-    z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0;
+    z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0;
   }
   if (td) {
     td_phase<RP, STATS>(P, L, items);
@@ -639,6 +876,16 @@ struct Kernels {
 }  // namespace
 
 // ------------------------------------------------------------------ host side
+
+// Dynamic shared memory of every kernel that can run a bottom-up level.
+static size_t dyn_smem_bytes(int threads_per_block) {
+  return sizeof(BuWarpSmem) * (size_t)(threads_per_block / 32);
+}
+
+static cudaError_t prepare_kernel(const void* fn, int threads_per_block) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)dyn_smem_bytes(threads_per_block));
+}
 
 static int resolve_policy(const bfs_graph* g, const bfs_params& p) {
   if (p.policy != BFS_POLICY_AUTO) return p.policy;
@@ -676,6 +923,7 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
   K.small_max = p.small_max;
   K.chunk = p.chunk;
   K.bu_warp_min = p.bu_warp_min;
+  K.bu_chunk = p.bu_chunk;
   K.need_qv = K.policy != BFS_POLICY_TD_ONLY;
   K.timeout_ns = (long long)p.timeout_ms * 1000000ll;
   K.barrier_extra = p.test_barrier_extra;
@@ -684,22 +932,26 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
 template <typename RP, bool STATS>
 static int launch_persistent(bfs_graph* g, KParams& K, const bfs_params& p, cudaStream_t stream) {
   void* fn = Kernels<RP, STATS>::persistent();
+  const size_t smem = dyn_smem_bytes(p.threads_per_block);
+  GBFS_CUDA(prepare_kernel(fn, p.threads_per_block));
   int per_sm = 0;
-  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, 0));
+  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, smem));
   if (per_sm < 1) return BFS_EINVAL;
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   dim3 grid((unsigned)(per_sm * g->num_sms)), block((unsigned)p.threads_per_block);
   void* args[] = {&K};
-  GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, 0, stream));
+  GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, stream));
   return BFS_OK;
 }
 
 template <typename RP, bool STATS>
 static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaStream_t stream) {
   SingleWs& ws = g->ws;
+  const size_t smem = dyn_smem_bytes(p.threads_per_block);
+  GBFS_CUDA(prepare_kernel(reinterpret_cast<void*>(&k_level<RP, STATS>), p.threads_per_block));
   int per_sm = 0;
   GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, reinterpret_cast<void*>(&k_level<RP, STATS>), p.threads_per_block, 0));
+      &per_sm, reinterpret_cast<void*>(&k_level<RP, STATS>), p.threads_per_block, smem));
   if (per_sm < 1) return BFS_EINVAL;
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   dim3 grid((unsigned)(per_sm * g->num_sms)), block((unsigned)p.threads_per_block);
@@ -714,7 +966,7 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
   bool td = true;
   Ctrl host_tot{};
   for (;;) {
-    k_level<RP, STATS><<<grid, block, 0, stream>>>(K, L, td ? 1 : 0, fb, items);
+    k_level<RP, STATS><<<grid, block, smem, stream>>>(K, L, td ? 1 : 0, fb, items);
     GBFS_CUDA(cudaGetLastError());
     if (td) ++tdl; else ++bul;
     GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,
@@ -787,15 +1039,17 @@ template <typename RP>
 static int launch_graph(bfs_graph* g, KParams& K, const bfs_params& p, cudaStream_t stream) {
   SingleWs& ws = g->ws;
   void* fn = Kernels<RP, false>::persistent();
+  const size_t smem = dyn_smem_bytes(p.threads_per_block);
+  GBFS_CUDA(prepare_kernel(fn, p.threads_per_block));
   int per_sm = 0;
-  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, 0));
+  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, smem));
   if (per_sm < 1) return BFS_EINVAL;
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   cudaKernelNodeParams kp{};
   kp.func = fn;
   kp.gridDim = dim3((unsigned)(per_sm * g->num_sms));
   kp.blockDim = dim3((unsigned)p.threads_per_block);
-  kp.sharedMemBytes = 0;
+  kp.sharedMemBytes = (unsigned)smem;
   void* args[] = {&K};
   kp.kernelParams = args;
   const int key = (per_sm * 4096 + p.threads_per_block) * 2 + (g->rp_bits == 32 ? 1 : 0);
@@ -833,12 +1087,14 @@ static int launch_graph(bfs_graph* g, KParams& K, const bfs_params& p, cudaStrea
 int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads_per_block,
                                cudaStream_t stream) {
   void* fn = rp_bits == 32 ? Kernels<int, false>::persistent() : Kernels<long long, false>::persistent();
+  const size_t smem = dyn_smem_bytes(threads_per_block);
+  GBFS_CUDA(prepare_kernel(fn, threads_per_block));
   int per_sm = 0;
-  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads_per_block, 0));
+  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads_per_block, smem));
   if (per_sm < 1) return BFS_EINVAL;
   dim3 grid((unsigned)(per_sm * num_sms)), block((unsigned)threads_per_block);
   void* args[] = {&K};
-  GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, 0, stream));
+  GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, stream));
   return BFS_OK;
 }
 
