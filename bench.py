@@ -204,7 +204,7 @@ def run_ours(args):
     rp, col, srcs = make_graph(args.scale)
     t_gen = time.perf_counter() - t_gen
     n, m = len(rp) - 1, len(col)
-    g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE)
+    g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER))
     params = bfs.make_params(policy=args.policy, launch=args.launch)
     stream = torch.cuda.Stream()
     dist_buf = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -285,6 +285,7 @@ def run_ours(args):
                    "row_ptr": "int64", "sources": len(srcs), "source_seed": SRC_SEED,
                    "policy": {0: "auto", 1: "frontier", 2: "edges", 3: "td_only"}.get(args.policy, str(args.policy)),
                    "launch": {0: "persistent", 1: "per_level", 2: "graph"}[args.launch],
+                   "adjacency_order": "id" if args.no_degree_order else "degree_desc",
                    "l2": "inputs larger than L2 (4.3 GB neighbour ids), no flush",
                    "step": "64 single-source BFS, each timed with CUDA events",
                    "graph_gen_s": round(t_gen, 1)},
@@ -322,6 +323,8 @@ def main(argv=None):
     ap.add_argument("--launch", type=int, default=0)
     ap.add_argument("--cpu-sample", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-degree-order", action="store_true",
+                    help="keep the generator's id-sorted adjacency order on the device")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

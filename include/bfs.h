@@ -51,6 +51,9 @@ extern "C" {
 #define BFS_DEVICE_PTRS 1      /* row_ptr / col_idx are device pointers (copied device-to-device) */
 #define BFS_VALIDATE 2         /* check row_ptr[0]==0, monotone row_ptr, row_ptr[n]==m, 0<=col<n */
 #define BFS_VALIDATE_SYMMETRY 4 /* also check that every arc (u,v) has its reverse (v,u) */
+#define BFS_DEGREE_ORDER 8     /* store each adjacency list highest-degree neighbour first (ties by
+                                  id); distances are unchanged, bottom-up scans stop sooner.
+                                  Needs m < 2^31 and temporary device memory of 16*m bytes. */
 
 /* ---- direction policies (bfs_params.policy) ----
  * Every policy yields the same distances; they differ only in work.
@@ -87,7 +90,7 @@ typedef struct bfs_params {
     int32_t small_max;       /* top-down: vertices with degree < small_max (<= 32) are expanded
                                 32 at a time by one warp; larger ones get a warp each (default 32) */
     int32_t chunk;           /* top-down: a vertex's adjacency is split into work items of at most
-                                `chunk` edges (256..65535, default 1024) */
+                                `chunk` edges (256..65535, default 256) */
     int32_t bu_warp_min;     /* bottom-up: an unvisited vertex with degree > bu_warp_min (<= 2^24) is
                                 scanned on its own by the whole warp; smaller ones share the warp's
                                 32-entry steps with their neighbours in the bitmap word (default 32) */
@@ -99,7 +102,10 @@ typedef struct bfs_params {
                                    were launched, so a wait runs out and BFS_ETIMEOUT is returned */
     int32_t bu_chunk;        /* bottom-up: groups of 32 bitmap words a warp takes per grab from a shared
                                 cursor (0 = static interleaved assignment; default 1) */
-    int32_t reserved[8];
+    int32_t bu_thread_max;   /* bottom-up: a vertex whose parent is not among its first aligned four
+                                entries keeps scanning on its own lane for up to this many more
+                                entries before the warp takes over (default 32) */
+    int32_t reserved[7];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique
@@ -153,8 +159,9 @@ void bfs_params_default(bfs_params *p);
  * The graph must be symmetric: the bottom-up phase (Listing 2) reads a
  * vertex's adjacency as its in-neighbours.  Self-loops and repeated entries
  * are allowed and do not change any distance.
- * Errors: BFS_EINVAL (null pointers, n < 1, n >= 2^31, m < 0, int32 offsets
- * with m >= 2^31, failed validation), BFS_ENOMEM, BFS_ECUDA.  Synchronous.
+ * Errors: BFS_EINVAL (null pointers, n < 1, n >= 2^31, m < 0, m >= 2^39, int32
+ * offsets with m >= 2^31, a degree >= 2^31 - 2^16, failed validation),
+ * BFS_ENOMEM, BFS_ECUDA.  Synchronous.
  */
 int bfs_graph_upload(const void *row_ptr, int row_ptr_bits, const int32_t *col_idx, int64_t n,
                      int64_t m, int flags, bfs_graph **out);
@@ -207,8 +214,8 @@ int bfs_single_ex(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *pa
  *        validated (it must be a valid symmetric CSR).
  *  src   source vertex in [0, n).
  *  dist  device int32[n] output (-1 = unreachable).
- * Limit: the scratch needs about 24.5*n + m/16 bytes (each of its nine regions
- * rounded up to 256 bytes); larger graphs get BFS_ENOMEM.
+ * Limit: the scratch needs about 24.5*n + m/15 bytes (each of its eleven
+ * regions rounded up to 256 bytes); larger graphs get BFS_ENOMEM.
  * The first call on each device looks up the array's device address (with
  * that device current); make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents: calls

@@ -33,6 +33,7 @@ BFS_HOST_PTRS = 0
 BFS_DEVICE_PTRS = 1
 BFS_VALIDATE = 2
 BFS_VALIDATE_SYMMETRY = 4
+BFS_DEGREE_ORDER = 8
 
 BFS_POLICY_AUTO = 0
 BFS_POLICY_FRONTIER = 1
@@ -60,7 +61,8 @@ class bfs_params(ctypes.Structure):
         ("small_max", ctypes.c_int32), ("chunk", ctypes.c_int32), ("bu_warp_min", ctypes.c_int32),
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("timeout_ms", ctypes.c_int32), ("script", ctypes.c_uint64),
-        ("test_barrier_extra", ctypes.c_int32), ("bu_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8),
+        ("test_barrier_extra", ctypes.c_int32), ("bu_chunk", ctypes.c_int32),
+        ("bu_thread_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
     ]
 
 

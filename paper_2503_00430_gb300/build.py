@@ -15,8 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-OBJDIR = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libbfs.so")
+# GBFS_BUILD_TAG builds a side variant (own object dir and library name), e.g.
+# together with NVCC_APPEND_FLAGS to compare compile-time settings.
+_TAG = os.environ.get("GBFS_BUILD_TAG", "")
+OBJDIR = os.path.join(HERE, "_build" + _TAG)
+LIB = os.path.join(HERE, f"libbfs{_TAG}.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -178,6 +178,7 @@ int ensure_single_ws(bfs_graph* g) {
     GBFS_CUDA(cudaMemset(ws.bm[i], 0, nwb));
     GBFS_CUDA(cudaMalloc(&ws.qv[i], sizeof(int) * (size_t)g->n));
     GBFS_CUDA(cudaMalloc(&ws.it[i], sizeof(unsigned long long) * (size_t)ws.cap));
+    GBFS_CUDA(cudaMalloc(&ws.mg[i], sizeof(MegaRec) * (size_t)(g->m / 8192 + 2)));
   }
   GBFS_CUDA(cudaMalloc(&ws.ctrl, sizeof(Ctrl)));
   GBFS_CUDA(cudaMemset(ws.ctrl, 0, sizeof(Ctrl)));
@@ -198,6 +199,7 @@ void free_single_ws(bfs_graph* g) {
     cudaFree(ws.bm[i]);
     cudaFree(ws.qv[i]);
     cudaFree(ws.it[i]);
+    cudaFree(ws.mg[i]);
   }
   cudaFree(ws.ctrl);
   cudaFree(ws.dist_tmp);
@@ -218,6 +220,7 @@ static int check_params(const bfs_params& p) {
   if (p.threads_per_block < 64 || p.threads_per_block > 1024 || (p.threads_per_block & 31)) return BFS_EINVAL;
   if (p.blocks_per_sm < 0 || p.timeout_ms < 1 || p.test_barrier_extra < 0) return BFS_EINVAL;
   if (p.bu_chunk < 0 || p.bu_chunk > 65536) return BFS_EINVAL;
+  if (p.bu_thread_max < 0 || p.bu_thread_max > (1 << 20)) return BFS_EINVAL;
   return BFS_OK;
 }
 
@@ -253,7 +256,7 @@ void bfs_params_default(bfs_params* p) {
   p->tau_inv = 20;
   p->large_diameter_degree = 7;
   p->small_max = 32;
-  p->chunk = 1024;
+  p->chunk = 256;
   p->bu_warp_min = 32;
   p->threads_per_block = 512;
   p->blocks_per_sm = 0;
@@ -261,6 +264,7 @@ void bfs_params_default(bfs_params* p) {
   p->script = 0;
   p->test_barrier_extra = 0;
   p->bu_chunk = 1;
+  p->bu_thread_max = 32;
 }
 
 int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n, int64_t m,
@@ -268,7 +272,7 @@ int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_i
   if (!out) return BFS_EINVAL;
   *out = nullptr;
   if (!row_ptr || (m > 0 && !col_idx)) return BFS_EINVAL;
-  if (n < 1 || n >= ((int64_t)1 << 31) || m < 0 || m >= ((int64_t)1 << 47)) return BFS_EINVAL;
+  if (n < 1 || n >= ((int64_t)1 << 31) || m < 0 || m >= ((int64_t)1 << 39)) return BFS_EINVAL;
   if (row_ptr_bits != 32 && row_ptr_bits != 64) return BFS_EINVAL;
   if (row_ptr_bits == 32 && m >= ((int64_t)1 << 31)) return BFS_EINVAL;
   const bool dev = (flags & BFS_DEVICE_PTRS) != 0;
@@ -296,6 +300,7 @@ int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_i
     if (e == cudaSuccess && m > 0) e = cudaMemcpy(g->col, col_idx, sizeof(int) * (size_t)m, kind);
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy (graph)", __FILE__, __LINE__); break; }
     rc = row_ptr_bits == 32 ? validate_and_facts<int>(g, flags) : validate_and_facts<long long>(g, flags);
+    if (rc == BFS_OK && (flags & BFS_DEGREE_ORDER)) rc = reorder_by_degree(g);
   } while (0);
   if (rc != BFS_OK) {
     release_graph(g);

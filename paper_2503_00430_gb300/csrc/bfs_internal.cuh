@@ -19,7 +19,17 @@ struct Slot {
   unsigned long long mf;     // sum of degrees over F_L
   unsigned long long nq;     // vertex-queue entries written by a bitmap -> queue conversion
   unsigned long long cursor; // bottom-up: next bitmap word to hand out (dynamic assignment)
+  unsigned long long mega;   // hub records: low 26 bits record count, high 38 bits chunk count
 };
+
+// A vertex whose adjacency spans more than 32 chunks ("hub"): one record, its
+// chunks handed out at the next top-down level as tickets base .. base+nch-1.
+struct MegaRec {
+  long long start;
+  long long deg;
+  unsigned long long base;
+};
+constexpr int kMegaCountBits = 26;
 
 // Device control block of one single-source query (zeroed before each launch).
 struct Ctrl {
@@ -49,12 +59,14 @@ struct KParams {
   unsigned long long* it0;
   unsigned long long* it1;
   long long cap;             // entries of it0 / it1
+  MegaRec* mg0;
+  MegaRec* mg1;
   Ctrl* ctrl;
   bfs_level_stat* lst;
   int lst_cap;
   int policy, alpha, beta, tau_inv;
   unsigned long long script;
-  int small_max, chunk, bu_warp_min, bu_chunk;
+  int small_max, chunk, bu_warp_min, bu_chunk, bu_thread_max;
   int need_qv;
   long long timeout_ns;
   int barrier_extra;
@@ -98,6 +110,7 @@ struct SingleWs {
   int* qv[2] = {nullptr, nullptr};
   unsigned long long* it[2] = {nullptr, nullptr};
   long long cap = 0;
+  MegaRec* mg[2] = {nullptr, nullptr};
   Ctrl* ctrl = nullptr;       // device
   Ctrl* h_ctrl = nullptr;     // pinned host mirror
   Slot* h_slot = nullptr;     // pinned, per-level launch mode
@@ -137,6 +150,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
   } while (0)
 
 bool is_device_pointer(const void* p);
+int reorder_by_degree(bfs_graph* g);
 int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,

@@ -41,7 +41,7 @@ size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for a graph with n vertices and m entries.
 struct Layout {
-  size_t ctrl, init_vis, vis, bm0, bm1, qv0, qv1, it0, it1, total;
+  size_t ctrl, init_vis, vis, bm0, bm1, qv0, qv1, it0, it1, mg0, mg1, total;
   long long cap;
 };
 
@@ -59,6 +59,8 @@ Layout layout_for(long long n, long long m) {
   L.qv1 = off; off += round256(sizeof(int) * (size_t)n);
   L.it0 = off; off += round256(sizeof(unsigned long long) * (size_t)L.cap);
   L.it1 = off; off += round256(sizeof(unsigned long long) * (size_t)L.cap);
+  L.mg0 = off; off += round256(sizeof(gbfs::MegaRec) * (size_t)(m / 8192 + 2));
+  L.mg1 = off; off += round256(sizeof(gbfs::MegaRec) * (size_t)(m / 8192 + 2));
   L.total = off;
   return L;
 }
@@ -137,6 +139,8 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   K.it0 = reinterpret_cast<unsigned long long*>(b + lay.it0);
   K.it1 = reinterpret_cast<unsigned long long*>(b + lay.it1);
   K.cap = lay.cap;
+  K.mg0 = reinterpret_cast<MegaRec*>(b + lay.mg0);
+  K.mg1 = reinterpret_cast<MegaRec*>(b + lay.mg1);
   K.ctrl = reinterpret_cast<Ctrl*>(b + lay.ctrl);
   K.lst = nullptr;
   K.lst_cap = 0;
@@ -150,6 +154,7 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   K.chunk = p.chunk;
   K.bu_warp_min = p.bu_warp_min;
   K.bu_chunk = p.bu_chunk;
+  K.bu_thread_max = p.bu_thread_max;
   K.need_qv = K.policy != BFS_POLICY_TD_ONLY;
   K.timeout_ns = (long long)p.timeout_ms * 1000000ll;
   K.barrier_extra = 0;

@@ -221,6 +221,11 @@ __device__ void seed_phase(const KParams& P) {
   if (d > 0 && d < P.small_max) {
     P.it0[0] = pack_item(s, (int)d);
     nsm = 1;
+  } else if (d >= P.small_max && (d + P.chunk - 1) / P.chunk > 32) {
+    P.mg0[0].start = s;
+    P.mg0[0].deg = d;
+    P.mg0[0].base = 0;
+    sl->mega = 1ull | ((unsigned long long)((d + P.chunk - 1) / P.chunk) << kMegaCountBits);
   } else if (d >= P.small_max) {
     for (long long c = 0; c * P.chunk < d; ++c) {
       long long len = d - c * P.chunk;
@@ -236,6 +241,38 @@ __device__ void seed_phase(const KParams& P) {
 
 // ---------------------------------------------------------------- top-down
 
+// Warp-collective: append hub records (vertices needing more than 32 chunks).
+// Lane-local candidates k with (mask >> k) & 1 get a record; one packed
+// atomic per warp hands out record slots and chunk tickets in the same order.
+__device__ __forceinline__ void append_hubs(const KParams& P, unsigned mask, const long long (&s)[4],
+                                            const int (&d)[4], Slot* out, MegaRec* mgn) {
+  int nrec = 0, nch = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if ((mask >> k) & 1u) {
+      ++nrec;
+      nch += (d[k] + P.chunk - 1) / P.chunk;
+    }
+  if (__ballot_sync(kFull, nrec != 0) == 0) return;
+  const int r_incl = warp_incl_scan(nrec), c_incl = warp_incl_scan(nch);
+  const int r_tot = __shfl_sync(kFull, r_incl, 31), c_tot = __shfl_sync(kFull, c_incl, 31);
+  unsigned long long b = 0;
+  if (lane_id() == 31)
+    b = atomicAdd(&out->mega, (unsigned long long)r_tot | ((unsigned long long)c_tot << kMegaCountBits));
+  b = __shfl_sync(kFull, b, 31);
+  unsigned long long r = (b & ((1ull << kMegaCountBits) - 1)) + (unsigned long long)(r_incl - nrec);
+  unsigned long long c = (b >> kMegaCountBits) + (unsigned long long)(c_incl - nch);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if ((mask >> k) & 1u) {
+      mgn[r].start = s[k];
+      mgn[r].deg = d[k];
+      mgn[r].base = c;
+      ++r;
+      c += (unsigned long long)((d[k] + P.chunk - 1) / P.chunk);
+    }
+}
+
 // Warp-collective: visit up to four neighbours per lane (c[k] < 0: none) at
 // level L.  All four visited words are read before any is claimed, all claims
 // (atomicOr on the bitmap word) are issued before any result is used, and the
@@ -246,7 +283,7 @@ __device__ void seed_phase(const KParams& P) {
 // warp.
 template <typename RP>
 __device__ __forceinline__ void td_visit4(const KParams& P, int L, const int (&c)[4], Slot* out, int* qvn,
-                                          unsigned long long* itn) {
+                                          unsigned long long* itn, MegaRec* mgn) {
   unsigned cur[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) cur[k] = c[k] >= 0 ? ld_relaxed_u32(P.vis + (c[k] >> 5)) : kFull;
@@ -276,11 +313,14 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, const int (&c
   const int ncl = __popc(cl);
   int nsm = 0, nlg = 0;
   unsigned long long dsum = 0;
+  unsigned hubs = 0;  // bit k: candidate k needs more than 32 chunks and gets a hub record
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if ((cl >> k) & 1u) {
+      const int ni = (d[k] + P.chunk - 1) / P.chunk;
       if (d[k] > 0 && d[k] < P.small_max) ++nsm;
-      else if (d[k] >= P.small_max) nlg += (d[k] + P.chunk - 1) / P.chunk;
+      else if (d[k] >= P.small_max && ni > 32) hubs |= 1u << k;
+      else if (d[k] >= P.small_max) nlg += ni;
       dsum += (unsigned long long)d[k];
     }
   }
@@ -305,13 +345,14 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, const int (&c
     if (P.need_qv) qvn[qi++] = c[k];
     if (d[k] > 0 && d[k] < P.small_max) {
       itn[si++] = pack_item(s[k], d[k]);
-    } else if (d[k] >= P.small_max) {
+    } else if (d[k] >= P.small_max && !((hubs >> k) & 1u)) {
       for (int o = 0; o < d[k]; o += P.chunk) {
         const int len = d[k] - o < P.chunk ? d[k] - o : P.chunk;
         itn[P.cap - 1 - (long long)(li++)] = pack_item(s[k] + o, len);
       }
     }
   }
+  append_hubs(P, hubs, s, d, out, mgn);
 }
 
 // Position of the n-th (0-based) set bit of mask, by halving the window with
@@ -343,10 +384,12 @@ __device__ __forceinline__ int owner_of(int excl, int e) {
 }
 
 template <typename RP, bool STATS>
-__device__ void td_phase(const KParams& P, int L, unsigned long long items_cur) {
+__device__ void td_phase(const KParams& P, int L, unsigned long long items_cur, unsigned long long mega_cur) {
   const unsigned long long nsmall = items_cur & 0xffffffffull, nlarge = items_cur >> 32;
   const unsigned long long* it = (L & 1) ? P.it1 : P.it0;
   unsigned long long* itn = (L & 1) ? P.it0 : P.it1;
+  const MegaRec* mg = (L & 1) ? P.mg1 : P.mg0;
+  MegaRec* mgn = (L & 1) ? P.mg0 : P.mg1;
   int* qvn = (L & 1) ? P.qv0 : P.qv1;
   Slot* out = &P.ctrl->slot[(L + 1) & 3];
   const unsigned lane = lane_id();
@@ -375,7 +418,7 @@ __device__ void td_phase(const KParams& P, int L, unsigned long long items_cur) 
         const int exo = __shfl_sync(kFull, excl, o);
         c[k] = e < total ? __ldg(P.col + so + (e - exo)) : -1;
       }
-      td_visit4<RP>(P, L, c, out, qvn, itn);
+      td_visit4<RP>(P, L, c, out, qvn, itn, mgn);
     }
   }
   // Large items (<= chunk edges each): one warp per item, 128-bit loads of the aligned span.
@@ -391,7 +434,36 @@ __device__ void td_phase(const KParams& P, int L, unsigned long long items_cur) 
       if (j < e) q = __ldg(reinterpret_cast<const int4*>(P.col + j));
       const int c[4] = {(j >= s && j < e) ? q.x : -1, (j + 1 >= s && j + 1 < e) ? q.y : -1,
                         (j + 2 >= s && j + 2 < e) ? q.z : -1, (j + 3 >= s && j + 3 < e) ? q.w : -1};
-      td_visit4<RP>(P, L, c, out, qvn, itn);
+      td_visit4<RP>(P, L, c, out, qvn, itn, mgn);
+    }
+  }
+  // Hub chunks: ticket t belongs to the last record whose base is <= t (a
+  // 32-way search over the records, which are ordered by base).
+  const long long nrec = (long long)(mega_cur & ((1ull << kMegaCountBits) - 1));
+  const long long nch = (long long)(mega_cur >> kMegaCountBits);
+  for (long long t = gw; t < nch; t += nwarps) {
+    long long lo = 0, hi = nrec;
+    while (hi - lo > 1) {
+      const long long step = (hi - lo + 31) / 32;
+      const long long idx = lo + (long long)lane * step;
+      const bool ok = idx < hi && (long long)mg[idx].base <= t;
+      const unsigned bm = __ballot_sync(kFull, ok);
+      const long long k = 31 - __clz(bm);
+      lo = lo + k * step;
+      hi = lo + step < hi ? lo + step : hi;
+    }
+    const long long o = (t - (long long)mg[lo].base) * P.chunk;
+    const long long hd = mg[lo].deg;
+    const long long s = mg[lo].start + o;
+    const long long e = s + (hd - o < P.chunk ? hd - o : P.chunk);
+    if (STATS && lane == 0) acc.edges += (unsigned long long)(e - s);
+    for (long long base = s & ~3ll; base < e; base += 128) {
+      const long long j = base + 4 * (long long)lane;
+      int4 q = make_int4(-1, -1, -1, -1);
+      if (j < e) q = __ldg(reinterpret_cast<const int4*>(P.col + j));
+      const int c[4] = {(j >= s && j < e) ? q.x : -1, (j + 1 >= s && j + 1 < e) ? q.y : -1,
+                        (j + 2 >= s && j + 2 < e) ? q.z : -1, (j + 3 >= s && j + 3 < e) ? q.w : -1};
+      td_visit4<RP>(P, L, c, out, qvn, itn, mgn);
     }
   }
   if (STATS) flush_acc<STATS>(P, L, acc, out, false);
@@ -404,7 +476,11 @@ __device__ __forceinline__ bool in_frontier(const unsigned* front, int u) {
 }
 
 // Shared-memory staging of one warp in a bottom-up batch.
-constexpr int kPendCap = 64;  // deferred long scans per warp (two rounds of 32 lanes)
+#ifndef GBFS_BU_U
+#define GBFS_BU_U 2
+#endif
+constexpr int kBuU = GBFS_BU_U;       // unvisited vertices per lane in flight in a bottom-up round
+constexpr int kPendCap = 32 * kBuU;   // deferred long scans per warp (one round's worth)
 struct BuWarpSmem {
   unsigned next[32];             // new-frontier bits of the batch's 32 words
   long long pstart[kPendCap];    // deferred scan: next entry to examine
@@ -436,11 +512,35 @@ __device__ void bu_drain(const KParams& P, int L, const unsigned* front, BuWarpS
   for (int g0 = 0; g0 < np; g0 += 32) {
     const int j = g0 + (int)lane;
     const bool have = j < np;
-    const long long ps = have ? sm.pstart[j] : 0;
-    const int pl = have ? sm.plen[j] : 0;
+    long long ps = have ? sm.pstart[j] : 0;  // 4-aligned
+    int pl = have ? sm.plen[j] : 0;
     const int pv = have ? sm.pv[j] : 0;
     const int pdeg = have ? sm.pd[j] : 0;
     int ex = have ? sm.pex[j] : 0;
+    // Each lane first continues its own vertex for up to bu_thread_max entries,
+    // one aligned 128-bit group (four probes in flight) at a time.
+    bool tfound = false;
+    for (int done = 0; pl > 0 && done < P.bu_thread_max; done += 4) {
+      const int4 q = __ldg(reinterpret_cast<const int4*>(P.col + ps));
+      const int c4[4] = {q.x, q.y, q.z, q.w};
+      bool h[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) h[t] = t < pl && ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u);
+      int ft = -1;
+#pragma unroll
+      for (int t = 3; t >= 0; --t)
+        if (h[t]) ft = t;
+      if (ft >= 0) {
+        tfound = true;
+        ex += ft + 1;
+        pl = 0;
+        break;
+      }
+      const int step = pl < 4 ? pl : 4;
+      ex += step;
+      pl -= step;
+      ps += 4;
+    }
     const bool heavy = pl > P.bu_warp_min;
     const int len = heavy ? 0 : pl;
     const int incl = warp_incl_scan(len);
@@ -490,8 +590,8 @@ __device__ void bu_drain(const KParams& P, int L, const unsigned* front, BuWarpS
       if (!pend) break;
       last = (int)__reduce_max_sync(kFull, (unsigned)(((pend >> lane) & 1u) ? incl : 0));
     }
-    bool found = (fnd >> lane) & 1u;
-    if (STATS && len > 0 && !found) ex += len;
+    bool found = tfound || ((fnd >> lane) & 1u);
+    if (STATS && len > 0 && !((fnd >> lane) & 1u)) ex += len;
     unsigned hv = __ballot_sync(kFull, heavy);
     while (hv) {
       const int h = __ffs(hv) - 1;
@@ -544,11 +644,11 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
   const int total = __shfl_sync(kFull, incl, 31);
   if (STATS) acc.unvisited += (unsigned long long)cnt;
   __syncwarp();
-  for (int r0 = 0; r0 < total; r0 += 64) {
-    int v[2];
-    long long s[2], e[2];
+  for (int r0 = 0; r0 < total; r0 += 32 * kBuU) {
+    int v[kBuU];
+    long long s[kBuU], e[kBuU];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kBuU; ++k) {
       const int kk = r0 + 32 * k + (int)lane;
       const int wo = owner_of(excl, kk);
       const unsigned aw = __shfl_sync(kFull, act, wo);
@@ -557,7 +657,7 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
       if (kk < total) v[k] = (int)((w0 + wo) * 32 + (long long)nth_set_bit(aw, kk - ew));
     }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kBuU; ++k) {
       s[k] = 0;
       e[k] = 0;
       if (v[k] >= 0) {
@@ -565,15 +665,15 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
         e[k] = rp_at<RP>(P.rp, (long long)v[k] + 1);
       }
     }
-    int4 q[2];
+    int4 q[kBuU];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kBuU; ++k) {
       q[k] = make_int4(0, 0, 0, 0);
       if (e[k] > s[k]) q[k] = __ldg(reinterpret_cast<const int4*>(P.col + (s[k] & ~3ll)));
     }
-    unsigned f[2][4];
+    unsigned f[kBuU][4];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kBuU; ++k) {
       const long long a0 = s[k] & ~3ll;
       const int c4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
 #pragma unroll
@@ -583,7 +683,7 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
       }
     }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kBuU; ++k) {
       if (v[k] < 0) continue;
       const long long a0 = s[k] & ~3ll;
       long long hit = -1;
@@ -607,14 +707,30 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
       }
     }
     __syncwarp();
-    if (sm.npend > kPendCap - 64) bu_drain<STATS>(P, L, front, sm, w0, acc);
+    if (sm.npend > 0) bu_drain<STATS>(P, L, front, sm, w0, acc);
   }
   if (sm.npend > 0) bu_drain<STATS>(P, L, front, sm, w0, acc);
   __syncwarp();
+  const unsigned nx = sm.next[lane];
   if (w < P.nw) {
-    const unsigned nx = sm.next[lane];
     next[w] = nx;
     if (nx) P.vis[w] = vw | nx;  // this warp is the only writer of its batch's words
+  }
+  // Vertex queue of the new frontier (read by a later change of direction).
+  const int fc = __popc(nx);
+  const int f_incl = warp_incl_scan(fc);
+  const int f_tot = __shfl_sync(kFull, f_incl, 31);
+  if (f_tot) {
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&P.ctrl->slot[(L + 1) & 3].nq, (unsigned long long)f_tot);
+    base = __shfl_sync(kFull, base, 31) + (unsigned long long)(f_incl - fc);
+    int* qvn = ((L + 1) & 1) ? P.qv1 : P.qv0;
+    unsigned t = nx;
+    while (t) {
+      const int b = __ffs(t) - 1;
+      t &= t - 1;
+      qvn[base++] = (int)(w * 32 + b);
+    }
   }
   __syncwarp();
 }
@@ -671,65 +787,50 @@ __device__ void scatter_phase(const int* qv, long long nv, unsigned* bm) {
   }
 }
 
-// Bitmap -> queue for one nonzero word: vertex queue entries and degree-binned
-// work items of the set bits.
+// Bottom-up -> top-down: the work items of F_{L+1} from its vertex queue
+// (written by the bottom-up level), one vertex per lane.
 template <typename RP>
-__device__ __forceinline__ void convert_word(const KParams& P, long long w, unsigned word, Slot* out, int* qvn,
-                                             unsigned long long* itn) {
-  const unsigned lane = lane_id();
-  const unsigned lt = lanemask_lt();
-  const bool mine = (word >> lane) & 1u;
-  const long long v = w * 32 + lane;
-  long long s = 0;
-  int d = 0;
-  if (mine) {
-    s = rp_at<RP>(P.rp, v);
-    d = (int)(rp_at<RP>(P.rp, v + 1) - s);
-  }
-  const int nsm = (mine && d > 0 && d < P.small_max) ? 1 : 0;
-  const int nlg = (mine && d >= P.small_max) ? (d + P.chunk - 1) / P.chunk : 0;
-  const unsigned smask = __ballot_sync(kFull, nsm);
-  const int lg_incl = warp_incl_scan(nlg);
-  const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
-  unsigned long long b_items = 0, b_q = 0;
-  if (lane == 0) {
-    b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
-    if (P.need_qv) b_q = atomicAdd(&out->nq, (unsigned long long)__popc(word));
-  }
-  b_items = __shfl_sync(kFull, b_items, 0);
-  b_q = __shfl_sync(kFull, b_q, 0);
-  if (mine && P.need_qv) qvn[b_q + __popc(word & lt)] = (int)v;
-  if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
-  if (nlg) {
-    unsigned long long b = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
-    for (int o = 0; o < d; o += P.chunk) {
-      const int len = d - o < P.chunk ? d - o : P.chunk;
-      itn[P.cap - 1 - (long long)(b++)] = pack_item(s + o, len);
-    }
-  }
-}
-
-// Bitmap -> queue: for the frontier F_{L+1} in bitmap `bm`, write the vertex
-// queue and the degree-binned work items of parity (L+1).  Words are read 32
-// at a time per warp; only nonzero ones are expanded.
-template <typename RP>
-__device__ void convert_phase(const KParams& P, int L, const unsigned* bm) {
+__device__ void convert_phase(const KParams& P, int L, long long nf) {
   const int Ln = L + 1;
   unsigned long long* itn = (Ln & 1) ? P.it1 : P.it0;
-  int* qvn = (Ln & 1) ? P.qv1 : P.qv0;
+  const int* qv = (Ln & 1) ? P.qv1 : P.qv0;
   Slot* out = &P.ctrl->slot[Ln & 3];
   const unsigned lane = lane_id();
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned lt = lanemask_lt();
+  const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nbatch = ((long long)P.nw + 31) / 32;
-  for (long long b = gw; b < nbatch; b += nwarps) {
-    const long long w = b * 32 + lane;
-    const unsigned word = w < P.nw ? bm[w] : 0u;
-    unsigned todo = __ballot_sync(kFull, word != 0u);
-    while (todo) {
-      const int i = __ffs(todo) - 1;
-      todo &= todo - 1;
-      convert_word<RP>(P, b * 32 + i, __shfl_sync(kFull, word, i), out, qvn, itn);
+  for (long long b0 = gw * 32; b0 < nf; b0 += nwarps * 32) {
+    const long long i = b0 + lane;
+    long long s = 0;
+    int d = 0;
+    if (i < nf) {
+      const int v = qv[i];
+      s = rp_at<RP>(P.rp, v);
+      d = (int)(rp_at<RP>(P.rp, (long long)v + 1) - s);
+    }
+    const int ni = (d + P.chunk - 1) / P.chunk;
+    const bool hub = d >= P.small_max && ni > 32;
+    const int nsm = (d > 0 && d < P.small_max) ? 1 : 0;
+    const int nlg = (d >= P.small_max && !hub) ? ni : 0;
+    {
+      const long long hs[4] = {s, 0, 0, 0};
+      const int hd[4] = {d, 0, 0, 0};
+      append_hubs(P, hub ? 1u : 0u, hs, hd, out, (Ln & 1) ? P.mg1 : P.mg0);
+    }
+    const unsigned smask = __ballot_sync(kFull, nsm);
+    const int lg_incl = warp_incl_scan(nlg);
+    const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
+    unsigned long long b_items = 0;
+    if (lane == 0)
+      b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
+    b_items = __shfl_sync(kFull, b_items, 0);
+    if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
+    if (nlg) {
+      unsigned long long bb = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
+      for (int o = 0; o < d; o += P.chunk) {
+        const int len = d - o < P.chunk ? d - o : P.chunk;
+        itn[P.cap - 1 - (long long)(bb++)] = pack_item(s + o, len);
+      }
     }
   }
 }
@@ -776,16 +877,17 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
   unsigned long long t_mark = STATS ? globaltimer_ns() : 0ull;
   st.edges_visited = (long long)ld_relaxed_u64(&P.ctrl->slot[0].mf);
   unsigned long long items = ld_relaxed_u64(&P.ctrl->slot[0].items);
+  unsigned long long mega = ld_relaxed_u64(&P.ctrl->slot[0].mega);
   int converted = 0, conversions = 0, tdl = 0, bul = 0;
   for (;;) {
     const int L = st.L;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       Slot* z = &P.ctrl->slot[(L + 2) & 3];
-      z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0;
+      z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0; z->mega = 0;
     }
     if (st.td) {
       ++tdl;
-      td_phase<RP, STATS>(P, L, items);
+      td_phase<RP, STATS>(P, L, items, mega);
     } else {
       ++bul;
       bu_phase<RP, STATS>(P, L, st.fb ? P.bm1 : P.bm0, st.fb ? P.bm0 : P.bm1);
@@ -810,8 +912,8 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
       st.fb = 0;
       converted = 1;
     } else if (!st.td && ntd) {
-      // bottom-up -> top-down: the bitmap just written becomes the queue and work items
-      convert_phase<RP>(P, L, st.fb ? P.bm0 : P.bm1);
+      // bottom-up -> top-down: work items from the new frontier's vertex queue
+      convert_phase<RP>(P, L, nf);
       if (!grid_barrier(P, epoch)) return;
       converted = 1;
     } else if (!st.td && !ntd) {
@@ -821,7 +923,10 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
       ++conversions;
       if (STATS && blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->conv_frontier += (unsigned long long)nf;
     }
-    if (ntd) items = ld_relaxed_u64(&nx->items);
+    if (ntd) {
+      items = ld_relaxed_u64(&nx->items);
+      mega = ld_relaxed_u64(&nx->mega);
+    }
     st.td = ntd;
     st.nf_cur = nf;
     st.L = L + 1;
@@ -845,13 +950,14 @@ __global__ void __launch_bounds__(1024) k_init_seed(KParams P) {
 }
 
 template <typename RP, bool STATS>
-__global__ void __launch_bounds__(1024) k_level(KParams P, int L, int td, int fb, unsigned long long items) {
+__global__ void __launch_bounds__(1024) k_level(KParams P, int L, int td, int fb, unsigned long long items,
+                                                unsigned long long mega) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Slot* z = &P.ctrl->slot[(L + 2) & 3];
-    z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0;
+    z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0; z->mega = 0;
   }
   if (td) {
-    td_phase<RP, STATS>(P, L, items);
+    td_phase<RP, STATS>(P, L, items, mega);
   } else {
     bu_phase<RP, STATS>(P, L, fb ? P.bm1 : P.bm0, fb ? P.bm0 : P.bm1);
   }
@@ -864,8 +970,8 @@ __global__ void __launch_bounds__(1024) k_scatter(const int* qv, long long nv, u
 }
 
 template <typename RP>
-__global__ void __launch_bounds__(1024) k_convert(KParams P, int L, const unsigned* bm) {
-  convert_phase<RP>(P, L, bm);
+__global__ void __launch_bounds__(1024) k_convert(KParams P, int L, long long nf) {
+  convert_phase<RP>(P, L, nf);
 }
 
 template <typename RP, bool STATS>
@@ -912,6 +1018,8 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
   K.it0 = ws.it[0];
   K.it1 = ws.it[1];
   K.cap = ws.cap;
+  K.mg0 = ws.mg[0];
+  K.mg1 = ws.mg[1];
   K.ctrl = ws.ctrl;
   K.lst = nullptr;
   K.lst_cap = 0;
@@ -924,6 +1032,7 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
   K.chunk = p.chunk;
   K.bu_warp_min = p.bu_warp_min;
   K.bu_chunk = p.bu_chunk;
+  K.bu_thread_max = p.bu_thread_max;
   K.need_qv = K.policy != BFS_POLICY_TD_ONLY;
   K.timeout_ns = (long long)p.timeout_ms * 1000000ll;
   K.barrier_extra = p.test_barrier_extra;
@@ -960,13 +1069,13 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
   GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[0], sizeof(Slot), cudaMemcpyDeviceToHost, stream));
   GBFS_CUDA(cudaStreamSynchronize(stream));
   long long edges_visited = (long long)ws.h_slot->mf;
-  unsigned long long items = ws.h_slot->items;
+  unsigned long long items = ws.h_slot->items, mega = ws.h_slot->mega;
   long long nf_cur = 1, reached = 1;
   int L = 0, fb = 0, tdl = 0, bul = 0, conversions = 0, converted = 0;
   bool td = true;
   Ctrl host_tot{};
   for (;;) {
-    k_level<RP, STATS><<<grid, block, smem, stream>>>(K, L, td ? 1 : 0, fb, items);
+    k_level<RP, STATS><<<grid, block, smem, stream>>>(K, L, td ? 1 : 0, fb, items, mega);
     GBFS_CUDA(cudaGetLastError());
     if (td) ++tdl; else ++bul;
     GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,
@@ -998,7 +1107,7 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
       fb = 0;
       converted = 1;
     } else if (!td && ntd) {
-      k_convert<RP><<<grid, block, 0, stream>>>(K, L, fb ? K.bm0 : K.bm1);
+      k_convert<RP><<<grid, block, 0, stream>>>(K, L, nf);
       GBFS_CUDA(cudaGetLastError());
       GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,
                                 stream));
@@ -1011,7 +1120,10 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
       ++conversions;
       host_tot.conv_frontier += (unsigned long long)nf;
     }
-    if (ntd) items = ws.h_slot->items;
+    if (ntd) {
+      items = ws.h_slot->items;
+      mega = ws.h_slot->mega;
+    }
     td = ntd;
     nf_cur = nf;
     ++L;

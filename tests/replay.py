@@ -67,10 +67,22 @@ def _ranges(starts, ends):
     return np.arange(tot, dtype=np.int64) + offs
 
 
-def replay(row_ptr, col, src, dist, policy=0, alpha=14, beta=24, tau_inv=20, script=0, large_diameter_degree=7):
+def degree_ordered(row_ptr, col):
+    """Each row reordered highest-degree neighbour first, ties by id (the layout of BFS_DEGREE_ORDER)."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    deg = np.diff(row_ptr)
+    owner = np.repeat(np.arange(len(row_ptr) - 1), deg)
+    return col[np.lexsort((col, -deg[col], owner))]
+
+
+def replay(row_ptr, col, src, dist, policy=0, alpha=14, beta=24, tau_inv=20, script=0, large_diameter_degree=7,
+           degree_order=False):
     """Expected bfs_stats totals and per-level records for ``dist``."""
     row_ptr = np.asarray(row_ptr, dtype=np.int64)
     col = np.asarray(col, dtype=np.int64)
+    if degree_order:
+        col = degree_ordered(row_ptr, col)
     n = len(row_ptr) - 1
     m = int(row_ptr[-1])
     deg = np.diff(row_ptr)

@@ -47,8 +47,10 @@ def run(B, g, src, n, stream=None, **kw):
     return dist.cpu().numpy(), st, lv
 
 
-def check(B, rp, col, srcs, rp_bits=64, policies=POLICIES, launches=(0, 1), extra=None, check_stats=True):
-    g = B.bfs_graph_upload(rp, col, flags=B.BFS_VALIDATE | B.BFS_VALIDATE_SYMMETRY, row_ptr_bits=rp_bits)
+def check(B, rp, col, srcs, rp_bits=64, policies=POLICIES, launches=(0, 1), extra=None, check_stats=True,
+          degree_order=False):
+    flags = B.BFS_VALIDATE | B.BFS_VALIDATE_SYMMETRY | (B.BFS_DEGREE_ORDER if degree_order else 0)
+    g = B.bfs_graph_upload(rp, col, flags=flags, row_ptr_bits=rp_bits)
     n = len(rp) - 1
     for src in srcs:
         want = oracle.bfs(rp, col, int(src))
@@ -58,7 +60,8 @@ def check(B, rp, col, srcs, rp_bits=64, policies=POLICIES, launches=(0, 1), extr
                 got, st, lv = run(B, g, src, n, **kw2)
                 assert np.array_equal(got, want), (name, launch, int(src), np.nonzero(got != want)[0][:10])
                 if check_stats:
-                    est, elv = replay(rp, col, int(src), want, policy=kw.get("policy", 0), script=kw.get("script", 0))
+                    est, elv = replay(rp, col, int(src), want, policy=kw.get("policy", 0), script=kw.get("script", 0),
+                                      degree_order=degree_order)
                     for k, v in est.items():
                         assert st[k] == v, (name, launch, k, st[k], v)
                     got_lv = [{k: v for k, v in x.items() if k != "ns"} for x in lv]
@@ -107,6 +110,9 @@ def test_er_and_rgg_and_grid(bfs):
     dict(bu_chunk=0),
     dict(bu_chunk=1, threads_per_block=64),
     dict(bu_chunk=4096),
+    dict(bu_thread_max=0),
+    dict(bu_thread_max=4, bu_warp_min=0),
+    dict(bu_thread_max=1 << 20, bu_warp_min=1 << 24),
 ])
 def test_parameter_extremes(bfs, params):
     rp, col = graphgen.rmat(13, seed=9)
@@ -190,3 +196,13 @@ def test_graph_info(bfs):
     g = bfs.bfs_graph_upload(rp, col)
     assert g.info() == {"n": 10, "m": 6, "max_degree": 3, "isolated": 6}
     g.free()
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_degree_ordered_layout(bfs, bits):
+    """BFS_DEGREE_ORDER changes only the scan order: same distances, counters of the reordered CSR."""
+    rp, col = graphgen.rmat(14, seed=11)
+    check(bfs, rp, col, graphgen.sources(rp, 3, 1006), rp_bits=bits, degree_order=True)
+    rp, col = G.star_graph(3000)
+    check(bfs, rp, col, [0, 5], rp_bits=bits, degree_order=True,
+          policies={k: POLICIES[k] for k in ("edges", "bu_from_1")})
