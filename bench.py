@@ -47,6 +47,24 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic():
+    """Per-launch DRAM traffic of the persistent kernel from the committed ncu
+    record, or None when the kernel's sources changed since it was captured."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "bfs_persistent_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return float(rec["traffic_bytes_per_launch_s25"])
+    except Exception:
+        return None
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -292,7 +310,7 @@ def run_ours(args):
         "latency": {"queries_per_s": len(secs) / float(np.sum(secs)), "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_kind": peak_kind, "traffic": None,
+                     "peak_kind": peak_kind, "traffic": measured_traffic() if args.scale == SCALE else None,
                      "kernel": "bfs_persistent_kernel<long long,false> (one launch per BFS)",
                      "bytes_per_bfs_mean": float(np.mean([p["bytes"] for p in per_src]))},
         "e2e": e2e,
@@ -315,7 +333,7 @@ def run_ours(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)
