@@ -105,7 +105,12 @@ typedef struct bfs_params {
     int32_t bu_thread_max;   /* bottom-up: a vertex whose parent is not among its first aligned four
                                 entries keeps scanning on its own lane for up to this many more
                                 entries before the warp takes over (default 32) */
-    int32_t reserved[7];
+    int32_t ms_lanes;        /* bfs_multi: sources per group (1..256, default 256) */
+    int32_t ms_ring;         /* bfs_multi: frontier levels kept before they are written out (2..8,
+                                default 8) */
+    int32_t ms_heavy_min;    /* bfs_multi pull levels: vertices with more entries are scanned by a
+                                whole warp (default 256) */
+    int32_t reserved[4];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique
@@ -138,6 +143,18 @@ typedef struct bfs_level_stat {
     int64_t ns;              /* persistent launch: device time from the end of the previous level
                                 (including any conversion) to the end of this one */
 } bfs_level_stat;
+
+/* Counters of one bfs_multi call (summed over its groups). */
+typedef struct bfs_multi_stats {
+    int32_t levels;          /* most levels of any group (largest eccentricity + 1) */
+    int32_t push_levels;     /* levels run in push (top-down) form, summed over groups */
+    int32_t pull_levels;     /* levels run in pull (bottom-up) form, summed over groups */
+    int32_t groups;          /* source groups of up to ms_lanes sources */
+    int64_t pushed_edges;    /* entries read by push levels */
+    int64_t pulled_edges;    /* entries read by pull levels */
+    int64_t output_bytes;    /* bytes written to dist (every output row counted per window) */
+    int64_t reserved[4];
+} bfs_multi_stats;
 
 /* Message for a BFS_* code (static string). */
 const char *bfs_strerror(int code);
@@ -195,6 +212,25 @@ int bfs_single(bfs_graph *g, int32_t src, int32_t *dist, void *stream);
  */
 int bfs_single_ex(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *params,
                   bfs_stats *stats, bfs_level_stat *levels, int32_t level_cap, void *stream);
+
+/*
+ * Distances from k sources at once (multi-source BFS: the level-synchronous
+ * loop of Section 2 run for up to 256 sources together, one bit per source in
+ * per-vertex masks; sparse levels push as in Listing 1, dense levels pull as in
+ * Listing 2's bottom-up scan).
+ *  srcs       host int32[k], each in [0, n); repeats allowed.
+ *  dist       [k][n] row-major (row i = distances from srcs[i]), device or host
+ *             memory (detected); dist_bits 8 (uint8, 255 = unreachable) or 32
+ *             (int32, -1 = unreachable).
+ * Sources are processed in groups of bfs_params.ms_lanes (default 256).
+ * Blocks until done.  Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ERANGE
+ * (uint8 output and a distance above 254: dist is then incomplete).
+ */
+int bfs_multi(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist_bits, void *stream);
+
+/* bfs_multi with parameters (NULL = defaults) and optional counters (NULL = none). */
+int bfs_multi_ex(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist_bits,
+                 const bfs_params *params, bfs_multi_stats *stats, void *stream);
 
 /*
  * bfs_single distances without any memory allocation (the paper has no

@@ -62,7 +62,8 @@ class bfs_params(ctypes.Structure):
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("timeout_ms", ctypes.c_int32), ("script", ctypes.c_uint64),
         ("test_barrier_extra", ctypes.c_int32), ("bu_chunk", ctypes.c_int32),
-        ("bu_thread_max", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("bu_thread_max", ctypes.c_int32), ("ms_lanes", ctypes.c_int32), ("ms_ring", ctypes.c_int32),
+        ("ms_heavy_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -73,6 +74,17 @@ class bfs_stats(ctypes.Structure):
         ("td_frontier", ctypes.c_int64), ("td_edges", ctypes.c_int64), ("bu_unvisited", ctypes.c_int64),
         ("bu_edges", ctypes.c_int64), ("bu_found", ctypes.c_int64), ("conv_frontier", ctypes.c_int64),
         ("reserved", ctypes.c_int64 * 4),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class bfs_multi_stats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32), ("push_levels", ctypes.c_int32), ("pull_levels", ctypes.c_int32),
+        ("groups", ctypes.c_int32), ("pushed_edges", ctypes.c_int64), ("pulled_edges", ctypes.c_int64),
+        ("output_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4),
     ]
 
     def as_dict(self) -> dict:
@@ -106,6 +118,9 @@ _SIGNATURES = [
     ("bfs_single_ex", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_stats),
                                      _vp, _i32, _vp]),
     ("bfs_single_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _i64, _i32, _vp, _vp]),
+    ("bfs_multi", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, _vp]),
+    ("bfs_multi_ex", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.POINTER(bfs_params),
+                                    ctypes.POINTER(bfs_multi_stats), _vp]),
 ]
 
 
@@ -269,3 +284,21 @@ def bfs_single_noalloc(row_ptr, col_idx, src: int, dist, stream=None):
     _check(load().bfs_single_noalloc(_ptr(row_ptr), bits, _ptr(col_idx) if m else None, n, m, int(src), _ptr(dist),
                                      _stream_handle(stream)), "bfs_single_noalloc")
     return dist
+
+
+def bfs_multi(g: Graph, srcs, dist, dist_bits: int = 32, stream=None):
+    """Distances from every source in ``srcs`` into ``dist`` ([k][n], uint8 or int32)."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.int32)
+    _check(load().bfs_multi(g.handle, _ptr(srcs), len(srcs), _ptr(dist), dist_bits, _stream_handle(stream)),
+           "bfs_multi")
+    return dist
+
+
+def bfs_multi_ex(g: Graph, srcs, dist, dist_bits: int = 32, params: bfs_params | None = None, stream=None) -> dict:
+    """bfs_multi with parameters; returns its counters."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.int32)
+    st = bfs_multi_stats()
+    _check(load().bfs_multi_ex(g.handle, _ptr(srcs), len(srcs), _ptr(dist), dist_bits,
+                               ctypes.byref(params) if params is not None else None, ctypes.byref(st),
+                               _stream_handle(stream)), "bfs_multi_ex")
+    return st.as_dict()

@@ -159,6 +159,7 @@ int validate_and_facts(bfs_graph* g, int flags) {
 void release_graph(bfs_graph* g) {
   if (!g) return;
   free_single_ws(g);
+  free_multi_ws(g);
   if (g->rp) cudaFree(g->rp);
   if (g->col) cudaFree(g->col);
   if (g->init_vis) cudaFree(g->init_vis);
@@ -221,6 +222,7 @@ static int check_params(const bfs_params& p) {
   if (p.blocks_per_sm < 0 || p.timeout_ms < 1 || p.test_barrier_extra < 0) return BFS_EINVAL;
   if (p.bu_chunk < 0 || p.bu_chunk > 65536) return BFS_EINVAL;
   if (p.bu_thread_max < 0 || p.bu_thread_max > (1 << 20)) return BFS_EINVAL;
+  if (p.ms_lanes < 1 || p.ms_lanes > 256 || p.ms_ring < 2 || p.ms_ring > 8 || p.ms_heavy_min < 0) return BFS_EINVAL;
   return BFS_OK;
 }
 
@@ -265,6 +267,9 @@ void bfs_params_default(bfs_params* p) {
   p->test_barrier_extra = 0;
   p->bu_chunk = 1;
   p->bu_thread_max = 32;
+  p->ms_lanes = 256;
+  p->ms_ring = 8;
+  p->ms_heavy_min = 256;
 }
 
 int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n, int64_t m,
@@ -355,6 +360,29 @@ int bfs_single_ex(bfs_graph* g, int32_t src, int32_t* dist, const bfs_params* pa
 
 int bfs_single(bfs_graph* g, int32_t src, int32_t* dist, void* stream) {
   return bfs_single_ex(g, src, dist, nullptr, nullptr, nullptr, 0, stream);
+}
+
+int bfs_multi_ex(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int dist_bits, const bfs_params* params,
+                 bfs_multi_stats* stats, void* stream) {
+  if (!g || !srcs || !dist || k <= 0) return BFS_EINVAL;
+  if (dist_bits != 8 && dist_bits != 32) return BFS_EINVAL;
+  for (int32_t i = 0; i < k; ++i)
+    if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return BFS_EINVAL;
+  bfs_params p;
+  if (params) {
+    p = *params;
+  } else {
+    bfs_params_default(&p);
+  }
+  int rc = check_params(p);
+  if (rc != BFS_OK) return rc;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  std::lock_guard<std::mutex> lock(g->mu);
+  return run_multi(g, srcs, k, dist, dist_bits, p, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int bfs_multi(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int dist_bits, void* stream) {
+  return bfs_multi_ex(g, srcs, k, dist, dist_bits, nullptr, nullptr, stream);
 }
 
 }  // extern "C"

@@ -126,6 +126,10 @@ struct SingleWs {
 
 }  // namespace gbfs
 
+namespace gbfs {
+struct MultiWs;
+}
+
 struct bfs_graph {
   long long n = 0, m = 0;
   int rp_bits = 64;
@@ -138,6 +142,7 @@ struct bfs_graph {
   long long max_deg = 0, isolated = 0;
   std::mutex mu;
   gbfs::SingleWs ws;
+  gbfs::MultiWs* ms = nullptr;  // multi-source workspace (bfs_multi.cu)
 };
 
 namespace gbfs {
@@ -155,6 +160,10 @@ int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
                bfs_level_stat* levels, int level_cap, cudaStream_t stream);
+int ensure_multi_ws(bfs_graph* g, int ring);
+void free_multi_ws(bfs_graph* g);
+int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, const bfs_params& p,
+              bfs_multi_stats* st, cudaStream_t s);
 int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads_per_block,
                                cudaStream_t stream);
 

@@ -1,0 +1,649 @@
+// Multi-source BFS: up to 256 sources per group, one bit per source ("lane")
+// in W = 1, 2 or 4 64-bit words per vertex.
+//
+// Per group and level L (the paper's level-synchronous loop, Section 2,
+// applied to 64*W searches at once):
+//   X[v]  lanes that have reached v;   F_L[v]  lanes that reached v at level L.
+//   push (sparse levels, Listing 1's top-down form): every frontier vertex u
+//     ORs F_L[u] & ~X[v] into an accumulator of each neighbour v; touched
+//     vertices are then applied: F_{L+1}[v] = acc & ~X[v], X[v] |= F_{L+1}[v];
+//   pull (dense levels, Listing 2's bottom-up form): every vertex not yet
+//     reached by all lanes ORs F_L[u] over its neighbours u and stops as soon
+//     as every lane is either known or found; F_{L+1}[v] = acc & ~X[v].
+// The direction follows the same edge-count rule as the single-source path.
+// Frontier masks of successive levels are kept in a ring of K arrays; a writer
+// pass turns them into dist[source][vertex] rows with whole-sector stores
+// (dist = the level whose frontier holds the lane's bit), so the output is
+// written once instead of byte by byte at every level.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bfs_internal.cuh"
+
+namespace gbfs {
+
+struct MsCtrl {
+  unsigned long long nf;        // vertices of the new frontier
+  unsigned long long mf;        // their degree sum
+  unsigned long long done_deg;  // degrees of vertices that became reached by every lane
+  unsigned long long nq;        // new frontier queue length
+  unsigned long long ntouch;    // push: touched vertices
+  unsigned long long nheavy;    // pull: deferred high-degree vertices
+  unsigned long long edges;     // entries examined (pull) or pushed (push)
+  unsigned long long pad;
+};
+
+struct MultiWs {
+  bool ready = false;
+  int ring = 0;                        // K
+  unsigned long long* X = nullptr;     // [n][4]
+  unsigned long long* acc = nullptr;   // [n][4] push accumulator (kept zero between levels)
+  unsigned long long* F = nullptr;     // [K][n][4]
+  unsigned* touched_bm = nullptr;      // [nw] (kept zero between levels)
+  int* q[2] = {nullptr, nullptr};      // frontier vertex queues
+  int* touched = nullptr;              // push: touched vertices
+  int* heavy = nullptr;                // pull: deferred vertices
+  int* d_src = nullptr;                // group sources
+  MsCtrl* ctrl = nullptr;
+  MsCtrl* h_ctrl = nullptr;            // pinned
+  void* staging = nullptr;             // host-output staging (one group)
+  size_t staging_bytes = 0;
+  cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+constexpr int kMsMaxRing = 8;
+
+__device__ __forceinline__ unsigned ms_lane() { return threadIdx.x & 31u; }
+
+template <typename RP>
+__device__ __forceinline__ long long rpv(const void* rp, long long i) {
+  return (long long)__ldg(reinterpret_cast<const RP*>(rp) + i);
+}
+
+template <int W>
+struct Mask {
+  unsigned long long w[W];
+};
+
+template <int W>
+__device__ __forceinline__ Mask<W> load_mask(const unsigned long long* p) {
+  Mask<W> m;
+  if constexpr (W == 4) {
+    const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
+    const ulonglong2 b = reinterpret_cast<const ulonglong2*>(p)[1];
+    m.w[0] = a.x; m.w[1] = a.y; m.w[2] = b.x; m.w[3] = b.y;
+  } else if constexpr (W == 2) {
+    const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
+    m.w[0] = a.x; m.w[1] = a.y;
+  } else {
+    m.w[0] = p[0];
+  }
+  return m;
+}
+
+template <int W>
+__device__ __forceinline__ void store_mask(unsigned long long* p, const Mask<W>& m) {
+  if constexpr (W == 4) {
+    reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(m.w[0], m.w[1]);
+    reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(m.w[2], m.w[3]);
+  } else if constexpr (W == 2) {
+    reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(m.w[0], m.w[1]);
+  } else {
+    p[0] = m.w[0];
+  }
+}
+
+struct MsArgs {
+  const void* rp;
+  const int* col;
+  long long n;
+  int nw;
+  unsigned long long full[4];   // lanes of the group
+  unsigned long long* X;
+  unsigned long long* acc;
+  const unsigned long long* Fcur;
+  unsigned long long* Fnext;
+  unsigned* touched_bm;
+  const int* qcur;
+  int* qnext;
+  int* touched;
+  int* heavy;
+  MsCtrl* ctrl;
+  int heavy_min;               // pull: vertices with more entries go to the warp-cooperative pass
+};
+
+template <int W>
+__device__ __forceinline__ bool is_full(const Mask<W>& m, const unsigned long long* full) {
+  bool f = true;
+#pragma unroll
+  for (int k = 0; k < W; ++k) f = f && (m.w[k] == full[k]);
+  return f;
+}
+
+template <int W>
+__device__ __forceinline__ bool is_zero(const Mask<W>& m) {
+  unsigned long long o = 0;
+#pragma unroll
+  for (int k = 0; k < W; ++k) o |= m.w[k];
+  return o == 0;
+}
+
+// Warp-aggregated append of v to a queue (flag: this lane appends).
+__device__ __forceinline__ void warp_append(bool flag, int v, unsigned long long* counter, int* q) {
+  const unsigned b = __ballot_sync(0xffffffffu, flag);
+  if (!b) return;
+  const int leader = __ffs(b) - 1;
+  unsigned long long base = 0;
+  if ((int)ms_lane() == leader) base = atomicAdd(counter, (unsigned long long)__popc(b));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  unsigned lt;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+  if (flag) q[base + __popc(b & lt)] = v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// ---- seed: lanes' sources into X and F_0, unique sources into the queue ----
+template <int W>
+__global__ void k_ms_seed(MsArgs A, const int* src, int lanes) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < lanes; i += gridDim.x * blockDim.x) {
+    const int s = src[i];
+    atomicOr(A.X + (long long)s * W + (i >> 6), 1ull << (i & 63));
+    atomicOr(const_cast<unsigned long long*>(A.Fcur) + (long long)s * W + (i >> 6), 1ull << (i & 63));
+  }
+}
+
+// ---- push: warp per frontier vertex, OR its new lanes into neighbours' accumulators ----
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned lane = ms_lane();
+  unsigned long long edges = 0;
+  for (long long qi = gw; qi < nq; qi += nwarps) {
+    const int u = A.qcur[qi];
+    const Mask<W> f = load_mask<W>(A.Fcur + (long long)u * W);
+    const long long s = rpv<RP>(A.rp, u), e = rpv<RP>(A.rp, (long long)u + 1);
+    if (lane == 0) edges += (unsigned long long)(e - s);
+    for (long long j0 = s; j0 < e; j0 += 32) {
+      const long long j = j0 + lane;
+      bool touch = false;
+      int v = 0;
+      if (j < e) {
+        v = __ldg(A.col + j);
+        const Mask<W> x = load_mask<W>(A.X + (long long)v * W);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const unsigned long long add = f.w[k] & ~x.w[k];
+          if (add) {
+            atomicOr(A.acc + (long long)v * W + k, add);
+            any = true;
+          }
+        }
+        if (any) {
+          const unsigned bit = 1u << (v & 31);
+          touch = !(atomicOr(A.touched_bm + (v >> 5), bit) & bit);
+        }
+      }
+      warp_append(touch, v, &A.ctrl->ntouch, A.touched);
+    }
+  }
+  if (lane == 0 && edges) atomicAdd(&A.ctrl->edges, edges);
+}
+
+// ---- apply after push: new lanes of touched vertices ----
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_apply(MsArgs A, long long nt) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  unsigned long long nf = 0, mf = 0, dd = 0;
+  for (long long base = tid - (tid & 31); base < nt; base += nth) {
+    const long long i = base + ms_lane();
+    bool in = i < nt;
+    int v = 0;
+    bool nz = false;
+    if (in) {
+      v = A.touched[i];
+      Mask<W> a = load_mask<W>(A.acc + (long long)v * W);
+      Mask<W> x = load_mask<W>(A.X + (long long)v * W);
+      Mask<W> nn, z;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        nn.w[k] = a.w[k] & ~x.w[k];
+        x.w[k] |= nn.w[k];
+        z.w[k] = 0;
+      }
+      store_mask<W>(A.acc + (long long)v * W, z);
+      store_mask<W>(A.X + (long long)v * W, x);
+      store_mask<W>(A.Fnext + (long long)v * W, nn);
+      atomicAnd(A.touched_bm + (v >> 5), ~(1u << (v & 31)));
+      nz = !is_zero<W>(nn);
+      if (nz) {
+        const long long d = rpv<RP>(A.rp, (long long)v + 1) - rpv<RP>(A.rp, v);
+        nf += 1;
+        mf += (unsigned long long)d;
+        if (is_full<W>(x, A.full)) dd += (unsigned long long)d;
+      }
+    }
+    warp_append(nz, v, &A.ctrl->nq, A.qnext);
+  }
+  nf = warp_sum(nf);
+  mf = warp_sum(mf);
+  dd = warp_sum(dd);
+  if (ms_lane() == 0) {
+    if (nf) atomicAdd(&A.ctrl->nf, nf);
+    if (mf) atomicAdd(&A.ctrl->mf, mf);
+    if (dd) atomicAdd(&A.ctrl->done_deg, dd);
+  }
+}
+
+// ---- pull: thread per vertex; high-degree vertices deferred to the warp pass ----
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  unsigned long long nf = 0, mf = 0, dd = 0, edges = 0;
+  for (long long base = tid - (tid & 31); base < A.n; base += nth) {
+    const long long v = base + ms_lane();
+    bool nz = false, defer = false;
+    if (v < A.n) {
+      Mask<W> x = load_mask<W>(A.X + v * W);
+      Mask<W> nn;
+#pragma unroll
+      for (int k = 0; k < W; ++k) nn.w[k] = 0;
+      if (!is_full<W>(x, A.full)) {
+        const long long s = rpv<RP>(A.rp, v), e = rpv<RP>(A.rp, v + 1);
+        if (e - s > A.heavy_min) {
+          defer = true;
+        } else {
+          Mask<W> acc;
+#pragma unroll
+          for (int k = 0; k < W; ++k) acc.w[k] = x.w[k];
+          long long j = s;
+          for (; j < e; ++j) {
+            const Mask<W> f = load_mask<W>(A.Fcur + (long long)__ldg(A.col + j) * W);
+#pragma unroll
+            for (int k = 0; k < W; ++k) acc.w[k] |= f.w[k];
+            if (is_full<W>(acc, A.full)) {
+              ++j;
+              break;
+            }
+          }
+          edges += (unsigned long long)(j - s);
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            nn.w[k] = acc.w[k] & ~x.w[k] & A.full[k];
+            x.w[k] |= nn.w[k];
+          }
+          nz = !is_zero<W>(nn);
+          if (nz) {
+            store_mask<W>(A.X + v * W, x);
+            nf += 1;
+            mf += (unsigned long long)(e - s);
+            if (is_full<W>(x, A.full)) dd += (unsigned long long)(e - s);
+          }
+        }
+      }
+      if (!defer) store_mask<W>(A.Fnext + v * W, nn);
+    }
+    warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
+    warp_append(defer, (int)v, &A.ctrl->nheavy, A.heavy);
+  }
+  nf = warp_sum(nf);
+  mf = warp_sum(mf);
+  dd = warp_sum(dd);
+  edges = warp_sum(edges);
+  if (ms_lane() == 0) {
+    if (nf) atomicAdd(&A.ctrl->nf, nf);
+    if (mf) atomicAdd(&A.ctrl->mf, mf);
+    if (dd) atomicAdd(&A.ctrl->done_deg, dd);
+    if (edges) atomicAdd(&A.ctrl->edges, edges);
+  }
+}
+
+// ---- pull, warp per deferred high-degree vertex: 32 neighbours per step ----
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_pull_heavy(MsArgs A, long long nh) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned lane = ms_lane();
+  unsigned long long edges = 0;
+  for (long long hi = gw; hi < nh; hi += nwarps) {
+    const int v = A.heavy[hi];
+    Mask<W> x = load_mask<W>(A.X + (long long)v * W);
+    const long long s = rpv<RP>(A.rp, v), e = rpv<RP>(A.rp, (long long)v + 1);
+    Mask<W> acc = x;
+    long long j0 = s;
+    for (; j0 < e; j0 += 32) {
+      const long long j = j0 + lane;
+      Mask<W> f;
+#pragma unroll
+      for (int k = 0; k < W; ++k) f.w[k] = 0;
+      if (j < e) f = load_mask<W>(A.Fcur + (long long)__ldg(A.col + j) * W);
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        unsigned long long t = f.w[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
+        acc.w[k] |= t;
+      }
+      if (is_full<W>(acc, A.full)) {
+        j0 += 32;
+        break;
+      }
+    }
+    if (lane == 0) edges += (unsigned long long)((j0 < e ? j0 : e) - s);
+    Mask<W> nn;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      nn.w[k] = acc.w[k] & ~x.w[k] & A.full[k];
+      x.w[k] |= nn.w[k];
+    }
+    const bool nz = !is_zero<W>(nn);
+    if (lane == 0) {
+      store_mask<W>(A.Fnext + (long long)v * W, nn);
+      if (nz) {
+        store_mask<W>(A.X + (long long)v * W, x);
+        atomicAdd(&A.ctrl->nf, 1ull);
+        atomicAdd(&A.ctrl->mf, (unsigned long long)(e - s));
+        if (is_full<W>(x, A.full)) atomicAdd(&A.ctrl->done_deg, (unsigned long long)(e - s));
+        const unsigned long long p = atomicAdd(&A.ctrl->nq, 1ull);
+        A.qnext[p] = v;
+      }
+    }
+  }
+  if (lane == 0 && edges) atomicAdd(&A.ctrl->edges, edges);
+}
+
+__global__ void k_ms_zero(unsigned long long* p, long long count) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < count; i += nth) p[i] = 0ull;
+}
+
+// ---- writer: ring levels [l0, l0 + nlev) into dist[row0 + i][v] ----
+// One block per tile of 32 vertices at a time: the tile's masks for all the
+// window's levels are staged in shared memory; thread i handles lane i and
+// writes that lane's 32 distances as one 32-byte (uint8) or 128-byte (int32)
+// run of its output row.  The first window also writes the "unreached" value
+// for lanes not found in it; later windows write only what they found.
+template <int W, typename T>
+__global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, long long n, int ring, int l0,
+                                                  int nlev, int lanes, bool first, T* dist, T unreached) {
+  __shared__ unsigned long long t[kMsMaxRing][32][W];
+  const long long ntiles = (n + 31) / 32;
+  const bool vec_ok = (n % 32) == 0 && (reinterpret_cast<uintptr_t>(dist) % 16) == 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long v0 = tile * 32;
+    for (int idx = threadIdx.x; idx < nlev * 32 * W; idx += blockDim.x) {
+      const int l = idx / (32 * W), r = idx % (32 * W);
+      const long long v = v0 + r / W;
+      const unsigned long long* slot = F + (long long)((l0 + l) % ring) * n * W;
+      t[l][r / W][r % W] = v < n ? slot[v * W + r % W] : 0ull;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < lanes; i += blockDim.x) {
+      const int w = i >> 6, b = i & 63;
+      T* row = dist + (long long)i * n + v0;
+      if (first && vec_ok && v0 + 32 <= n) {
+        T vals[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          T val = unreached;
+          for (int l = nlev - 1; l >= 0; --l)
+            if ((t[l][j][w] >> b) & 1ull) val = (T)(l0 + l);
+          vals[j] = val;
+        }
+        uint4* o = reinterpret_cast<uint4*>(row);
+#pragma unroll
+        for (int q = 0; q < (int)(32 * sizeof(T) / 16); ++q) o[q] = reinterpret_cast<const uint4*>(vals)[q];
+      } else {
+        for (int j = 0; j < 32 && v0 + j < n; ++j) {
+          int lv = -1;
+          for (int l = nlev - 1; l >= 0; --l)
+            if ((t[l][j][w] >> b) & 1ull) lv = l;
+          if (lv >= 0) row[j] = (T)(l0 + lv);
+          else if (first) row[j] = unreached;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename RP>
+__global__ void k_ms_degree_sum(const RP* rp, const int* src, int k, unsigned long long* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const int s = src[i];
+    atomicAdd(out, (unsigned long long)(rp[s + 1] - rp[s]));
+  }
+}
+
+}  // namespace
+
+int ensure_multi_ws(bfs_graph* g, int ring) {
+  if (!g->ms) g->ms = new MultiWs();
+  MultiWs& ws = *g->ms;
+  if (ws.ready && ws.ring == ring) return BFS_OK;
+  if (ws.ready) free_multi_ws(g), g->ms = new MultiWs();
+  MultiWs& w2 = *g->ms;
+  const size_t n = (size_t)g->n;
+  GBFS_CUDA(cudaMalloc(&w2.X, sizeof(unsigned long long) * 4 * n));
+  GBFS_CUDA(cudaMalloc(&w2.acc, sizeof(unsigned long long) * 4 * n));
+  GBFS_CUDA(cudaMemset(w2.acc, 0, sizeof(unsigned long long) * 4 * n));
+  GBFS_CUDA(cudaMalloc(&w2.F, sizeof(unsigned long long) * 4 * n * (size_t)ring));
+  GBFS_CUDA(cudaMalloc(&w2.touched_bm, sizeof(unsigned) * (size_t)g->nw));
+  GBFS_CUDA(cudaMemset(w2.touched_bm, 0, sizeof(unsigned) * (size_t)g->nw));
+  for (int i = 0; i < 2; ++i) GBFS_CUDA(cudaMalloc(&w2.q[i], sizeof(int) * n));
+  GBFS_CUDA(cudaMalloc(&w2.touched, sizeof(int) * n));
+  GBFS_CUDA(cudaMalloc(&w2.heavy, sizeof(int) * n));
+  GBFS_CUDA(cudaMalloc(&w2.d_src, sizeof(int) * 256));
+  GBFS_CUDA(cudaMalloc(&w2.ctrl, sizeof(MsCtrl)));
+  GBFS_CUDA(cudaMallocHost(&w2.h_ctrl, sizeof(MsCtrl)));
+  GBFS_CUDA(cudaEventCreateWithFlags(&w2.done, cudaEventDisableTiming));
+  w2.ring = ring;
+  w2.ready = true;
+  return BFS_OK;
+}
+
+void free_multi_ws(bfs_graph* g) {
+  if (!g->ms) return;
+  MultiWs& ws = *g->ms;
+  if (ws.done) cudaEventSynchronize(ws.done);
+  cudaFree(ws.X);
+  cudaFree(ws.acc);
+  cudaFree(ws.F);
+  cudaFree(ws.touched_bm);
+  cudaFree(ws.q[0]);
+  cudaFree(ws.q[1]);
+  cudaFree(ws.touched);
+  cudaFree(ws.heavy);
+  cudaFree(ws.d_src);
+  cudaFree(ws.ctrl);
+  cudaFree(ws.staging);
+  if (ws.h_ctrl) cudaFreeHost(ws.h_ctrl);
+  if (ws.done) cudaEventDestroy(ws.done);
+  delete g->ms;
+  g->ms = nullptr;
+}
+
+namespace {
+
+template <int W, typename RP, typename T>
+int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, int max_level, const bfs_params& p,
+              bfs_multi_stats* st, cudaStream_t s) {
+  MultiWs& ws = *g->ms;
+  const long long n = g->n;
+  const int grid = g->num_sms * 8, block = 256;
+  MsArgs A{};
+  A.rp = g->rp;
+  A.col = g->col;
+  A.n = n;
+  A.nw = g->nw;
+  for (int k = 0; k < 4; ++k) {
+    const int lo = 64 * k;
+    A.full[k] = lanes >= lo + 64 ? ~0ull : (lanes > lo ? ((1ull << (lanes - lo)) - 1ull) : 0ull);
+  }
+  A.X = ws.X;
+  A.acc = ws.acc;
+  A.touched_bm = ws.touched_bm;
+  A.touched = ws.touched;
+  A.heavy = ws.heavy;
+  A.ctrl = ws.ctrl;
+  A.heavy_min = p.ms_heavy_min;
+  const int K = ws.ring;
+  auto slot = [&](int l) { return ws.F + (long long)(l % K) * n * W; };
+  // Unique sources form the level-0 frontier queue.
+  std::vector<int> uniq(srcs, srcs + lanes);
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  GBFS_CUDA(cudaMemcpyAsync(ws.d_src, srcs, sizeof(int) * (size_t)lanes, cudaMemcpyHostToDevice, s));
+  GBFS_CUDA(cudaMemcpyAsync(ws.q[0], uniq.data(), sizeof(int) * uniq.size(), cudaMemcpyHostToDevice, s));
+  k_ms_zero<<<grid, block, 0, s>>>(ws.X, n * W);
+  k_ms_zero<<<grid, block, 0, s>>>(slot(0), n * W);
+  A.Fcur = slot(0);
+  k_ms_seed<W><<<1, 256, 0, s>>>(A, ws.d_src, lanes);
+  GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(MsCtrl), s));
+  k_ms_degree_sum<RP><<<1, 256, 0, s>>>(reinterpret_cast<const RP*>(g->rp), ws.q[0], (int)uniq.size(), &ws.ctrl->mf);
+  GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
+  GBFS_CUDA(cudaStreamSynchronize(s));
+  long long nf = (long long)uniq.size(), mf = (long long)ws.h_ctrl->mf, nf_prev = nf;
+  long long m_unfinished = g->m;
+  bool push = true;
+  int L = 0, flushed = 0, qc = 0;
+  bool first_flush = true;
+  int rc = BFS_OK;
+  auto flush = [&](int upto) -> int {  // write levels [flushed, upto]
+    const int nlev = upto - flushed + 1;
+    if (nlev <= 0) return BFS_OK;
+    k_ms_write<W, T><<<g->num_sms * 16, 256, 0, s>>>(ws.F, n, K, flushed, nlev, lanes, first_flush, dist, unreached);
+    GBFS_CUDA(cudaGetLastError());
+    first_flush = false;
+    flushed = upto + 1;
+    if (st) st->output_bytes += (long long)sizeof(T) * (long long)lanes * n;
+    return BFS_OK;
+  };
+  for (;;) {
+    // Direction for this level (edge-count rule, Section 2's BFS-Hybrid-dagger).
+    if (L > 0) {
+      if (push) push = !((long long)p.alpha * mf > m_unfinished);
+      else push = (long long)p.beta * nf < n && nf < nf_prev;
+    }
+    if (L + 1 - flushed >= K) {
+      rc = flush(L);
+      if (rc != BFS_OK) return rc;
+    }
+    unsigned long long* Fn = slot(L + 1);
+    A.Fcur = slot(L);
+    A.Fnext = Fn;
+    A.qcur = ws.q[qc];
+    A.qnext = ws.q[qc ^ 1];
+    GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(MsCtrl), s));
+    if (push) {
+      k_ms_zero<<<grid, block, 0, s>>>(Fn, n * W);
+      k_ms_push<W, RP><<<grid, block, 0, s>>>(A, nf);
+      GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
+      GBFS_CUDA(cudaStreamSynchronize(s));
+      const long long nt = (long long)ws.h_ctrl->ntouch;
+      if (st) st->pushed_edges += (long long)ws.h_ctrl->edges;
+      if (nt > 0) k_ms_apply<W, RP><<<grid, block, 0, s>>>(A, nt);
+      if (st) ++st->push_levels;
+    } else {
+      k_ms_pull<W, RP><<<grid, block, 0, s>>>(A);
+      GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
+      GBFS_CUDA(cudaStreamSynchronize(s));
+      const long long nh = (long long)ws.h_ctrl->nheavy;
+      if (nh > 0) k_ms_pull_heavy<W, RP><<<grid, block, 0, s>>>(A, nh);
+      if (st) ++st->pull_levels;
+    }
+    GBFS_CUDA(cudaGetLastError());
+    GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
+    GBFS_CUDA(cudaStreamSynchronize(s));
+    const MsCtrl c = *ws.h_ctrl;
+    if (st && !push) st->pulled_edges += (long long)c.edges;
+    nf_prev = nf;
+    nf = (long long)c.nf;
+    mf = (long long)c.mf;
+    m_unfinished -= (long long)c.done_deg;
+    if (nf == 0) break;
+    if (L + 1 > max_level) return BFS_ERANGE;
+    ++L;
+    qc ^= 1;
+  }
+  if (st && L + 1 > st->levels) st->levels = L + 1;
+  rc = flush(L);
+  if (rc != BFS_OK) return rc;
+  GBFS_CUDA(cudaEventRecord(ws.done, s));
+  return BFS_OK;
+}
+
+template <int W>
+int run_group_w(bfs_graph* g, const int* srcs, int lanes, void* dist, int bits, const bfs_params& p,
+                bfs_multi_stats* st, cudaStream_t s) {
+  if (bits == 8) {
+    if (g->rp_bits == 32)
+      return run_group<W, int, uint8_t>(g, srcs, lanes, (uint8_t*)dist, (uint8_t)255, 254, p, st, s);
+    return run_group<W, long long, uint8_t>(g, srcs, lanes, (uint8_t*)dist, (uint8_t)255, 254, p, st, s);
+  }
+  if (g->rp_bits == 32)
+    return run_group<W, int, int32_t>(g, srcs, lanes, (int32_t*)dist, -1, 0x7fffffff, p, st, s);
+  return run_group<W, long long, int32_t>(g, srcs, lanes, (int32_t*)dist, -1, 0x7fffffff, p, st, s);
+}
+
+}  // namespace
+
+int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, const bfs_params& p,
+              bfs_multi_stats* st, cudaStream_t s) {
+  int ring = p.ms_ring;
+  if (ring < 2) ring = 2;
+  if (ring > kMsMaxRing) ring = kMsMaxRing;
+  int rc = ensure_multi_ws(g, ring);
+  if (rc != BFS_OK) return rc;
+  MultiWs& ws = *g->ms;
+  GBFS_CUDA(cudaStreamWaitEvent(s, ws.done, 0));
+  const bool host_out = !is_device_pointer(dist);
+  const size_t esz = (size_t)bits / 8;
+  const int per_group = p.ms_lanes;
+  for (int g0 = 0; g0 < k; g0 += per_group) {
+    const int lanes = std::min(per_group, k - g0);
+    void* out = host_out ? nullptr : (void*)((char*)dist + (size_t)g0 * (size_t)g->n * esz);
+    if (host_out) {
+      const size_t need = (size_t)lanes * (size_t)g->n * esz;
+      if (ws.staging_bytes < need) {
+        cudaFree(ws.staging);
+        ws.staging = nullptr;
+        ws.staging_bytes = 0;
+        GBFS_CUDA(cudaMalloc(&ws.staging, need));
+        ws.staging_bytes = need;
+      }
+      out = ws.staging;
+    }
+    const int W = (lanes + 63) / 64;
+    if (W == 1) rc = run_group_w<1>(g, srcs + g0, lanes, out, bits, p, st, s);
+    else if (W == 2) rc = run_group_w<2>(g, srcs + g0, lanes, out, bits, p, st, s);
+    else rc = run_group_w<4>(g, srcs + g0, lanes, out, bits, p, st, s);
+    if (rc != BFS_OK) return rc;
+    if (st) ++st->groups;
+    if (host_out) {
+      GBFS_CUDA(cudaMemcpyAsync((char*)dist + (size_t)g0 * (size_t)g->n * esz, out,
+                                (size_t)lanes * (size_t)g->n * esz, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  GBFS_CUDA(cudaEventRecord(ws.done, s));
+  GBFS_CUDA(cudaStreamSynchronize(s));
+  return BFS_OK;
+}
+
+}  // namespace gbfs
