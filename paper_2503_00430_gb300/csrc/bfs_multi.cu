@@ -36,7 +36,19 @@ struct MsCtrl {
   unsigned long long nheavy;    // pull: deferred high-degree vertices
   unsigned long long edges;     // entries examined (pull) or pushed (push)
   unsigned long long pad;
+  unsigned long long act[4];    // lanes present in the new frontier
 };
+
+// A pull vertex with more entries than ms_heavy_min: its adjacency is cut into
+// chunks of kMsChunk entries, handed out as tickets base .. base+chunks-1.
+struct MsHeavy {
+  long long start;
+  long long deg;
+  unsigned long long base;
+  long long v;
+};
+constexpr int kMsChunk = 2048;
+constexpr int kMsCountBits = 32;
 
 struct MultiWs {
   bool ready = false;
@@ -47,7 +59,7 @@ struct MultiWs {
   unsigned* touched_bm = nullptr;      // [nw] (kept zero between levels)
   int* q[2] = {nullptr, nullptr};      // frontier vertex queues
   int* touched = nullptr;              // push: touched vertices
-  int* heavy = nullptr;                // pull: deferred vertices
+  MsHeavy* heavy = nullptr;            // pull: deferred high-degree vertices
   int* d_src = nullptr;                // group sources
   MsCtrl* ctrl = nullptr;
   MsCtrl* h_ctrl = nullptr;            // pinned
@@ -106,6 +118,7 @@ struct MsArgs {
   long long n;
   int nw;
   unsigned long long full[4];   // lanes of the group
+  unsigned long long act[4];    // lanes present in the current frontier (the only ones that can advance)
   unsigned long long* X;
   unsigned long long* acc;
   const unsigned long long* Fcur;
@@ -114,7 +127,7 @@ struct MsArgs {
   const int* qcur;
   int* qnext;
   int* touched;
-  int* heavy;
+  MsHeavy* heavy;
   MsCtrl* ctrl;
   int heavy_min;               // pull: vertices with more entries go to the warp-cooperative pass
 };
@@ -125,6 +138,27 @@ __device__ __forceinline__ bool is_full(const Mask<W>& m, const unsigned long lo
 #pragma unroll
   for (int k = 0; k < W; ++k) f = f && (m.w[k] == full[k]);
   return f;
+}
+
+// Every lane of `act` is set in m (lanes outside act cannot change this level).
+template <int W>
+__device__ __forceinline__ bool covers(const Mask<W>& m, const unsigned long long* act) {
+  bool f = true;
+#pragma unroll
+  for (int k = 0; k < W; ++k) f = f && ((m.w[k] & act[k]) == act[k]);
+  return f;
+}
+
+// OR of the new frontier lanes into the level's active-lane record (one atomic per warp and word).
+template <int W>
+__device__ __forceinline__ void warp_or_active(const Mask<W>& nn, MsCtrl* ctrl) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    unsigned long long t = nn.w[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31u) == 0 && t) atomicOr(&ctrl->act[k], t);
+  }
 }
 
 template <int W>
@@ -214,11 +248,14 @@ __global__ void __launch_bounds__(256) k_ms_apply(MsArgs A, long long nt) {
     bool in = i < nt;
     int v = 0;
     bool nz = false;
+    Mask<W> nn;
+#pragma unroll
+    for (int k = 0; k < W; ++k) nn.w[k] = 0;
     if (in) {
       v = A.touched[i];
       Mask<W> a = load_mask<W>(A.acc + (long long)v * W);
       Mask<W> x = load_mask<W>(A.X + (long long)v * W);
-      Mask<W> nn, z;
+      Mask<W> z;
 #pragma unroll
       for (int k = 0; k < W; ++k) {
         nn.w[k] = a.w[k] & ~x.w[k];
@@ -238,6 +275,7 @@ __global__ void __launch_bounds__(256) k_ms_apply(MsArgs A, long long nt) {
       }
     }
     warp_append(nz, v, &A.ctrl->nq, A.qnext);
+    warp_or_active<W>(nn, A.ctrl);
   }
   nf = warp_sum(nf);
   mf = warp_sum(mf);
@@ -258,30 +296,46 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
   for (long long base = tid - (tid & 31); base < A.n; base += nth) {
     const long long v = base + ms_lane();
     bool nz = false, defer = false;
+    long long sv = 0, dv = 0;
+    Mask<W> nn;
+#pragma unroll
+    for (int k = 0; k < W; ++k) nn.w[k] = 0;
     if (v < A.n) {
       Mask<W> x = load_mask<W>(A.X + v * W);
-      Mask<W> nn;
-#pragma unroll
-      for (int k = 0; k < W; ++k) nn.w[k] = 0;
-      if (!is_full<W>(x, A.full)) {
+      if (!covers<W>(x, A.act)) {
         const long long s = rpv<RP>(A.rp, v), e = rpv<RP>(A.rp, v + 1);
         if (e - s > A.heavy_min) {
           defer = true;
+          sv = s;
+          dv = e - s;
         } else {
           Mask<W> acc;
 #pragma unroll
           for (int k = 0; k < W; ++k) acc.w[k] = x.w[k];
-          long long j = s;
-          for (; j < e; ++j) {
-            const Mask<W> f = load_mask<W>(A.Fcur + (long long)__ldg(A.col + j) * W);
+          // Aligned groups of four entries: one 128-bit load, then the four
+          // neighbours' masks are gathered together before they are combined.
+          long long j0 = s & ~3ll;
+          for (; j0 < e; j0 += 4) {
+            const int4 q = __ldg(reinterpret_cast<const int4*>(A.col + j0));
+            const int c4[4] = {q.x, q.y, q.z, q.w};
+            Mask<W> f[4];
 #pragma unroll
-            for (int k = 0; k < W; ++k) acc.w[k] |= f.w[k];
-            if (is_full<W>(acc, A.full)) {
-              ++j;
+            for (int t = 0; t < 4; ++t) {
+              if (j0 + t >= s && j0 + t < e) {
+                f[t] = load_mask<W>(A.Fcur + (long long)c4[t] * W);
+              } else {
+#pragma unroll
+                for (int k = 0; k < W; ++k) f[t].w[k] = 0;
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < W; ++k) acc.w[k] |= f[0].w[k] | f[1].w[k] | f[2].w[k] | f[3].w[k];
+            if (covers<W>(acc, A.act)) {
+              j0 += 4;
               break;
             }
           }
-          edges += (unsigned long long)(j - s);
+          edges += (unsigned long long)((j0 < e ? j0 : e) - (s > (s & ~3ll) ? s : s));
 #pragma unroll
           for (int k = 0; k < W; ++k) {
             nn.w[k] = acc.w[k] & ~x.w[k] & A.full[k];
@@ -299,7 +353,35 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
       if (!defer) store_mask<W>(A.Fnext + v * W, nn);
     }
     warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
-    warp_append(defer, (int)v, &A.ctrl->nheavy, A.heavy);
+    {
+      // Deferred vertices: one record each; one packed atomic per warp hands
+      // out record slots and chunk tickets in the same order.
+      const int nch = defer ? (int)((dv + kMsChunk - 1) / kMsChunk) : 0;
+      const unsigned dm = __ballot_sync(0xffffffffu, defer);
+      if (dm) {
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o);
+          if ((int)ms_lane() >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long b = 0;
+        if (ms_lane() == 31)
+          b = atomicAdd(&A.ctrl->nheavy, (unsigned long long)__popc(dm) | ((unsigned long long)tot << kMsCountBits));
+        b = __shfl_sync(0xffffffffu, b, 31);
+        if (defer) {
+          unsigned lt;
+          asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+          MsHeavy& r = A.heavy[(b & ((1ull << kMsCountBits) - 1)) + __popc(dm & lt)];
+          r.start = sv;
+          r.deg = dv;
+          r.base = (b >> kMsCountBits) + (unsigned long long)(incl - nch);
+          r.v = v;
+        }
+      }
+    }
+    warp_or_active<W>(nn, A.ctrl);
   }
   nf = warp_sum(nf);
   mf = warp_sum(mf);
@@ -313,58 +395,127 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
   }
 }
 
-// ---- pull, warp per deferred high-degree vertex: 32 neighbours per step ----
+// ---- pull, deferred high-degree vertices: warp per chunk ticket ----
+// Ticket t belongs to the last record whose base is <= t (32-way search).  The
+// warp ORs the neighbours' frontier masks of its chunk, 128 entries per step
+// (four gathers in flight per lane), stops once the vertex's pending active
+// lanes are all covered, and ORs the new lanes into the vertex's accumulator.
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_pull_heavy(MsArgs A, long long nh) {
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(256) k_ms_heavy_chunks(MsArgs A, long long nrec, long long nch) {
+  const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const unsigned lane = ms_lane();
   unsigned long long edges = 0;
-  for (long long hi = gw; hi < nh; hi += nwarps) {
-    const int v = A.heavy[hi];
-    Mask<W> x = load_mask<W>(A.X + (long long)v * W);
-    const long long s = rpv<RP>(A.rp, v), e = rpv<RP>(A.rp, (long long)v + 1);
-    Mask<W> acc = x;
-    long long j0 = s;
-    for (; j0 < e; j0 += 32) {
-      const long long j = j0 + lane;
-      Mask<W> f;
+  for (long long t = gw; t < nch; t += nwarps) {
+    long long lo = 0, hi = nrec;
+    while (hi - lo > 1) {
+      const long long step = (hi - lo + 31) / 32;
+      const long long idx = lo + (long long)lane * step;
+      const bool ok = idx < hi && (long long)A.heavy[idx].base <= t;
+      const unsigned bm = __ballot_sync(0xffffffffu, ok);
+      lo += (long long)(31 - __clz(bm)) * step;
+      hi = lo + step < hi ? lo + step : hi;
+    }
+    const MsHeavy r = A.heavy[lo];
+    const long long cs = r.start + (t - (long long)r.base) * kMsChunk;
+    const long long ce = cs + (r.deg - (cs - r.start) < kMsChunk ? r.deg - (cs - r.start) : kMsChunk);
+    const Mask<W> x = load_mask<W>(A.X + r.v * W);
+    Mask<W> have = load_mask<W>(A.acc + r.v * W);
 #pragma unroll
-      for (int k = 0; k < W; ++k) f.w[k] = 0;
-      if (j < e) f = load_mask<W>(A.Fcur + (long long)__ldg(A.col + j) * W);
+    for (int k = 0; k < W; ++k) have.w[k] |= x.w[k];
+    if (covers<W>(have, A.act)) continue;
+    Mask<W> acc;
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc.w[k] = 0;
+    long long base = cs & ~3ll;
+    for (; base < ce; base += 128) {
+      const long long j = base + 4 * (long long)lane;
+      int4 q = make_int4(0, 0, 0, 0);
+      if (j < ce) q = __ldg(reinterpret_cast<const int4*>(A.col + j));
+      const int c4[4] = {q.x, q.y, q.z, q.w};
+      Mask<W> f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (j + u >= cs && j + u < ce) {
+          f[u] = load_mask<W>(A.Fcur + (long long)c4[u] * W);
+        } else {
+#pragma unroll
+          for (int k = 0; k < W; ++k) f[u].w[k] = 0;
+        }
+      }
 #pragma unroll
       for (int k = 0; k < W; ++k) {
-        unsigned long long t = f.w[k];
+        unsigned long long o = f[0].w[k] | f[1].w[k] | f[2].w[k] | f[3].w[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
-        acc.w[k] |= t;
+        for (int sh = 16; sh > 0; sh >>= 1) o |= __shfl_xor_sync(0xffffffffu, o, sh);
+        acc.w[k] |= o;
       }
-      if (is_full<W>(acc, A.full)) {
-        j0 += 32;
+      Mask<W> tot;
+#pragma unroll
+      for (int k = 0; k < W; ++k) tot.w[k] = acc.w[k] | have.w[k];
+      if (covers<W>(tot, A.act)) {
+        base += 128;
         break;
       }
     }
-    if (lane == 0) edges += (unsigned long long)((j0 < e ? j0 : e) - s);
-    Mask<W> nn;
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      nn.w[k] = acc.w[k] & ~x.w[k] & A.full[k];
-      x.w[k] |= nn.w[k];
-    }
-    const bool nz = !is_zero<W>(nn);
     if (lane == 0) {
-      store_mask<W>(A.Fnext + (long long)v * W, nn);
-      if (nz) {
-        store_mask<W>(A.X + (long long)v * W, x);
-        atomicAdd(&A.ctrl->nf, 1ull);
-        atomicAdd(&A.ctrl->mf, (unsigned long long)(e - s));
-        if (is_full<W>(x, A.full)) atomicAdd(&A.ctrl->done_deg, (unsigned long long)(e - s));
-        const unsigned long long p = atomicAdd(&A.ctrl->nq, 1ull);
-        A.qnext[p] = v;
+      edges += (unsigned long long)((base < ce ? base : ce) - cs);
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const unsigned long long add = acc.w[k] & ~have.w[k];
+        if (add) atomicOr(A.acc + r.v * W + k, add);
       }
     }
   }
   if (lane == 0 && edges) atomicAdd(&A.ctrl->edges, edges);
+}
+
+// ---- apply the deferred vertices' accumulators ----
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_heavy_apply(MsArgs A, long long nrec) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  unsigned long long nf = 0, mf = 0, dd = 0;
+  for (long long base = tid - (tid & 31); base < nrec; base += nth) {
+    const long long i = base + ms_lane();
+    bool nz = false;
+    long long v = 0;
+    Mask<W> nn;
+#pragma unroll
+    for (int k = 0; k < W; ++k) nn.w[k] = 0;
+    if (i < nrec) {
+      const MsHeavy r = A.heavy[i];
+      v = r.v;
+      const Mask<W> a = load_mask<W>(A.acc + v * W);
+      Mask<W> x = load_mask<W>(A.X + v * W);
+      Mask<W> z;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        nn.w[k] = a.w[k] & ~x.w[k] & A.full[k];
+        x.w[k] |= nn.w[k];
+        z.w[k] = 0;
+      }
+      store_mask<W>(A.acc + v * W, z);
+      store_mask<W>(A.Fnext + v * W, nn);
+      nz = !is_zero<W>(nn);
+      if (nz) {
+        store_mask<W>(A.X + v * W, x);
+        nf += 1;
+        mf += (unsigned long long)r.deg;
+        if (is_full<W>(x, A.full)) dd += (unsigned long long)r.deg;
+      }
+    }
+    warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
+    warp_or_active<W>(nn, A.ctrl);
+  }
+  nf = warp_sum(nf);
+  mf = warp_sum(mf);
+  dd = warp_sum(dd);
+  if (ms_lane() == 0) {
+    if (nf) atomicAdd(&A.ctrl->nf, nf);
+    if (mf) atomicAdd(&A.ctrl->mf, mf);
+    if (dd) atomicAdd(&A.ctrl->done_deg, dd);
+  }
 }
 
 __global__ void k_ms_zero(unsigned long long* p, long long count) {
@@ -383,6 +534,9 @@ template <int W, typename T>
 __global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, long long n, int ring, int l0,
                                                   int nlev, int lanes, bool first, T* dist, T unreached) {
   __shared__ unsigned long long t[kMsMaxRing][32][W];
+  // Per (vertex, word): lanes found in the window and the three bits of the
+  // offset of the level that found them (bit-sliced over the 64 lanes).
+  __shared__ unsigned long long pl[4][32][W];
   const long long ntiles = (n + 31) / 32;
   const bool vec_ok = (n % 32) == 0 && (reinterpret_cast<uintptr_t>(dist) % 16) == 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -394,28 +548,51 @@ __global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, l
       t[l][r / W][r % W] = v < n ? slot[v * W + r % W] : 0ull;
     }
     __syncthreads();
+    for (int idx = threadIdx.x; idx < 32 * W; idx += blockDim.x) {
+      const int j = idx / W, w = idx % W;
+      unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0;
+      for (int l = nlev - 1; l >= 0; --l) {
+        const unsigned long long m = t[l][j][w];
+        f |= m;
+        p0 = (p0 & ~m) | ((l & 1) ? m : 0ull);
+        p1 = (p1 & ~m) | ((l & 2) ? m : 0ull);
+        p2 = (p2 & ~m) | ((l & 4) ? m : 0ull);
+      }
+      pl[0][j][w] = f;
+      pl[1][j][w] = p0;
+      pl[2][j][w] = p1;
+      pl[3][j][w] = p2;
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < lanes; i += blockDim.x) {
       const int w = i >> 6, b = i & 63;
       T* row = dist + (long long)i * n + v0;
       if (first && vec_ok && v0 + 32 <= n) {
-        T vals[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          T val = unreached;
-          for (int l = nlev - 1; l >= 0; --l)
-            if ((t[l][j][w] >> b) & 1ull) val = (T)(l0 + l);
-          vals[j] = val;
-        }
         uint4* o = reinterpret_cast<uint4*>(row);
+        constexpr int kPer = 16 / (int)sizeof(T);  // values per 16-byte store
 #pragma unroll
-        for (int q = 0; q < (int)(32 * sizeof(T) / 16); ++q) o[q] = reinterpret_cast<const uint4*>(vals)[q];
+        for (int q = 0; q < 32 / kPer; ++q) {
+          unsigned wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+          for (int r = 0; r < kPer; ++r) {
+            const int j = q * kPer + r;
+            const int lv = (int)(((pl[1][j][w] >> b) & 1ull) | (((pl[2][j][w] >> b) & 1ull) << 1) |
+                                 (((pl[3][j][w] >> b) & 1ull) << 2));
+            const T val = ((pl[0][j][w] >> b) & 1ull) ? (T)(l0 + lv) : unreached;
+            if (sizeof(T) == 1) wd[r / 4] |= (unsigned)(uint8_t)val << (8 * (r % 4));
+            else wd[r] = (unsigned)val;
+          }
+          o[q] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        }
       } else {
         for (int j = 0; j < 32 && v0 + j < n; ++j) {
-          int lv = -1;
-          for (int l = nlev - 1; l >= 0; --l)
-            if ((t[l][j][w] >> b) & 1ull) lv = l;
-          if (lv >= 0) row[j] = (T)(l0 + lv);
-          else if (first) row[j] = unreached;
+          if ((pl[0][j][w] >> b) & 1ull) {
+            const int lv = (int)(((pl[1][j][w] >> b) & 1ull) | (((pl[2][j][w] >> b) & 1ull) << 1) |
+                                 (((pl[3][j][w] >> b) & 1ull) << 2));
+            row[j] = (T)(l0 + lv);
+          } else if (first) {
+            row[j] = unreached;
+          }
         }
       }
     }
@@ -448,7 +625,7 @@ int ensure_multi_ws(bfs_graph* g, int ring) {
   GBFS_CUDA(cudaMemset(w2.touched_bm, 0, sizeof(unsigned) * (size_t)g->nw));
   for (int i = 0; i < 2; ++i) GBFS_CUDA(cudaMalloc(&w2.q[i], sizeof(int) * n));
   GBFS_CUDA(cudaMalloc(&w2.touched, sizeof(int) * n));
-  GBFS_CUDA(cudaMalloc(&w2.heavy, sizeof(int) * n));
+  GBFS_CUDA(cudaMalloc(&w2.heavy, sizeof(MsHeavy) * (n + 2)));
   GBFS_CUDA(cudaMalloc(&w2.d_src, sizeof(int) * 256));
   GBFS_CUDA(cudaMalloc(&w2.ctrl, sizeof(MsCtrl)));
   GBFS_CUDA(cudaMallocHost(&w2.h_ctrl, sizeof(MsCtrl)));
@@ -495,6 +672,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   for (int k = 0; k < 4; ++k) {
     const int lo = 64 * k;
     A.full[k] = lanes >= lo + 64 ? ~0ull : (lanes > lo ? ((1ull << (lanes - lo)) - 1ull) : 0ull);
+    A.act[k] = A.full[k];
   }
   A.X = ws.X;
   A.acc = ws.acc;
@@ -564,8 +742,12 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
       k_ms_pull<W, RP><<<grid, block, 0, s>>>(A);
       GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
       GBFS_CUDA(cudaStreamSynchronize(s));
-      const long long nh = (long long)ws.h_ctrl->nheavy;
-      if (nh > 0) k_ms_pull_heavy<W, RP><<<grid, block, 0, s>>>(A, nh);
+      const unsigned long long hv = ws.h_ctrl->nheavy;
+      const long long nrec = (long long)(hv & ((1ull << kMsCountBits) - 1)), nch = (long long)(hv >> kMsCountBits);
+      if (nrec > 0) {
+        k_ms_heavy_chunks<W, RP><<<grid, block, 0, s>>>(A, nrec, nch);
+        k_ms_heavy_apply<W, RP><<<grid, block, 0, s>>>(A, nrec);
+      }
       if (st) ++st->pull_levels;
     }
     GBFS_CUDA(cudaGetLastError());
@@ -573,6 +755,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
     GBFS_CUDA(cudaStreamSynchronize(s));
     const MsCtrl c = *ws.h_ctrl;
     if (st && !push) st->pulled_edges += (long long)c.edges;
+    for (int k = 0; k < 4; ++k) A.act[k] = c.act[k];
     nf_prev = nf;
     nf = (long long)c.nf;
     mf = (long long)c.mf;
