@@ -110,7 +110,9 @@ typedef struct bfs_params {
                                 default 8) */
     int32_t ms_heavy_min;    /* bfs_multi pull levels: vertices with more entries are scanned by a
                                 whole warp (default 256) */
-    int32_t reserved[4];
+    int32_t ms_degree_order; /* bfs_multi pull levels visit vertices by decreasing degree (1, default)
+                                or by id (0) */
+    int32_t reserved[3];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique

@@ -156,6 +156,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
 bool is_device_pointer(const void* p);
 int reorder_by_degree(bfs_graph* g);
+int vertices_by_degree(bfs_graph* g, int* order);
 int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,

@@ -61,6 +61,7 @@ struct MultiWs {
   int* touched = nullptr;              // push: touched vertices
   MsHeavy* heavy = nullptr;            // pull: deferred high-degree vertices
   int* d_src = nullptr;                // group sources
+  int* order = nullptr;                // vertex ids by degree, highest first
   MsCtrl* ctrl = nullptr;
   MsCtrl* h_ctrl = nullptr;            // pinned
   void* staging = nullptr;             // host-output staging (one group)
@@ -128,6 +129,7 @@ struct MsArgs {
   int* qnext;
   int* touched;
   MsHeavy* heavy;
+  const int* order;
   MsCtrl* ctrl;
   int heavy_min;               // pull: vertices with more entries go to the warp-cooperative pass
 };
@@ -294,7 +296,8 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long nf = 0, mf = 0, dd = 0, edges = 0;
   for (long long base = tid - (tid & 31); base < A.n; base += nth) {
-    const long long v = base + ms_lane();
+    const long long oi = base + ms_lane();
+    const long long v = (A.order && oi < A.n) ? (long long)A.order[oi] : oi;
     bool nz = false, defer = false;
     long long sv = 0, dv = 0;
     Mask<W> nn;
@@ -530,69 +533,63 @@ __global__ void k_ms_zero(unsigned long long* p, long long count) {
 // writes that lane's 32 distances as one 32-byte (uint8) or 128-byte (int32)
 // run of its output row.  The first window also writes the "unreached" value
 // for lanes not found in it; later windows write only what they found.
+// Tile of kWt vertices: per (word, vertex) the lanes found in the window and
+// the three bits of the finding level's offset (bit-sliced over 64 lanes) go
+// to shared memory, vertex index innermost; then each warp writes one output
+// row segment at a time, lane j covering vertices j, j+32, j+64, j+96, so
+// every store instruction covers consecutive vertices of one row.
+constexpr int kWt = 128;
+
 template <int W, typename T>
 __global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, long long n, int ring, int l0,
                                                   int nlev, int lanes, bool first, T* dist, T unreached) {
-  __shared__ unsigned long long t[kMsMaxRing][32][W];
-  // Per (vertex, word): lanes found in the window and the three bits of the
-  // offset of the level that found them (bit-sliced over the 64 lanes).
-  __shared__ unsigned long long pl[4][32][W];
-  const long long ntiles = (n + 31) / 32;
-  const bool vec_ok = (n % 32) == 0 && (reinterpret_cast<uintptr_t>(dist) % 16) == 0;
+  __shared__ unsigned long long pl[4][W][kWt];
+  __shared__ unsigned long long tile_or[W];
+  const long long ntiles = (n + kWt - 1) / kWt;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long v0 = tile * 32;
-    for (int idx = threadIdx.x; idx < nlev * 32 * W; idx += blockDim.x) {
-      const int l = idx / (32 * W), r = idx % (32 * W);
-      const long long v = v0 + r / W;
-      const unsigned long long* slot = F + (long long)((l0 + l) % ring) * n * W;
-      t[l][r / W][r % W] = v < n ? slot[v * W + r % W] : 0ull;
-    }
+    const long long v0 = tile * kWt;
+    if (threadIdx.x < W) tile_or[threadIdx.x] = 0ull;
     __syncthreads();
-    for (int idx = threadIdx.x; idx < 32 * W; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < kWt * W; idx += blockDim.x) {
       const int j = idx / W, w = idx % W;
+      const long long v = v0 + j;
       unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0;
-      for (int l = nlev - 1; l >= 0; --l) {
-        const unsigned long long m = t[l][j][w];
-        f |= m;
-        p0 = (p0 & ~m) | ((l & 1) ? m : 0ull);
-        p1 = (p1 & ~m) | ((l & 2) ? m : 0ull);
-        p2 = (p2 & ~m) | ((l & 4) ? m : 0ull);
+      if (v < n) {
+        unsigned long long m[kMsMaxRing];
+#pragma unroll
+        for (int l = 0; l < kMsMaxRing; ++l)
+          m[l] = l < nlev ? F[(long long)((l0 + l) % ring) * n * W + v * W + w] : 0ull;
+#pragma unroll
+        for (int l = kMsMaxRing - 1; l >= 0; --l) {
+          f |= m[l];
+          p0 = (p0 & ~m[l]) | ((l & 1) ? m[l] : 0ull);
+          p1 = (p1 & ~m[l]) | ((l & 2) ? m[l] : 0ull);
+          p2 = (p2 & ~m[l]) | ((l & 4) ? m[l] : 0ull);
+        }
       }
-      pl[0][j][w] = f;
-      pl[1][j][w] = p0;
-      pl[2][j][w] = p1;
-      pl[3][j][w] = p2;
+      pl[0][w][j] = f;
+      pl[1][w][j] = p0;
+      pl[2][w][j] = p1;
+      pl[3][w][j] = p2;
+      if (!first && f) atomicOr(&tile_or[w], f);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < lanes; i += blockDim.x) {
+    for (int i = (int)warp; i < lanes; i += (int)nwarp) {
       const int w = i >> 6, b = i & 63;
+      if (!first && !((tile_or[w] >> b) & 1ull)) continue;
       T* row = dist + (long long)i * n + v0;
-      if (first && vec_ok && v0 + 32 <= n) {
-        uint4* o = reinterpret_cast<uint4*>(row);
-        constexpr int kPer = 16 / (int)sizeof(T);  // values per 16-byte store
 #pragma unroll
-        for (int q = 0; q < 32 / kPer; ++q) {
-          unsigned wd[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-          for (int r = 0; r < kPer; ++r) {
-            const int j = q * kPer + r;
-            const int lv = (int)(((pl[1][j][w] >> b) & 1ull) | (((pl[2][j][w] >> b) & 1ull) << 1) |
-                                 (((pl[3][j][w] >> b) & 1ull) << 2));
-            const T val = ((pl[0][j][w] >> b) & 1ull) ? (T)(l0 + lv) : unreached;
-            if (sizeof(T) == 1) wd[r / 4] |= (unsigned)(uint8_t)val << (8 * (r % 4));
-            else wd[r] = (unsigned)val;
-          }
-          o[q] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-        }
-      } else {
-        for (int j = 0; j < 32 && v0 + j < n; ++j) {
-          if ((pl[0][j][w] >> b) & 1ull) {
-            const int lv = (int)(((pl[1][j][w] >> b) & 1ull) | (((pl[2][j][w] >> b) & 1ull) << 1) |
-                                 (((pl[3][j][w] >> b) & 1ull) << 2));
-            row[j] = (T)(l0 + lv);
-          } else if (first) {
-            row[j] = unreached;
-          }
+      for (int r = 0; r < kWt / 32; ++r) {
+        const int j = (int)lane + 32 * r;
+        if (v0 + j >= n) break;
+        const bool fnd = (pl[0][w][j] >> b) & 1ull;
+        if (fnd) {
+          const int lv = (int)(((pl[1][w][j] >> b) & 1ull) | (((pl[2][w][j] >> b) & 1ull) << 1) |
+                               (((pl[3][w][j] >> b) & 1ull) << 2));
+          row[j] = (T)(l0 + lv);
+        } else if (first) {
+          row[j] = unreached;
         }
       }
     }
@@ -627,6 +624,11 @@ int ensure_multi_ws(bfs_graph* g, int ring) {
   GBFS_CUDA(cudaMalloc(&w2.touched, sizeof(int) * n));
   GBFS_CUDA(cudaMalloc(&w2.heavy, sizeof(MsHeavy) * (n + 2)));
   GBFS_CUDA(cudaMalloc(&w2.d_src, sizeof(int) * 256));
+  GBFS_CUDA(cudaMalloc(&w2.order, sizeof(int) * n));
+  {
+    const int rc = vertices_by_degree(g, w2.order);
+    if (rc != BFS_OK) return rc;
+  }
   GBFS_CUDA(cudaMalloc(&w2.ctrl, sizeof(MsCtrl)));
   GBFS_CUDA(cudaMallocHost(&w2.h_ctrl, sizeof(MsCtrl)));
   GBFS_CUDA(cudaEventCreateWithFlags(&w2.done, cudaEventDisableTiming));
@@ -648,6 +650,7 @@ void free_multi_ws(bfs_graph* g) {
   cudaFree(ws.touched);
   cudaFree(ws.heavy);
   cudaFree(ws.d_src);
+  cudaFree(ws.order);
   cudaFree(ws.ctrl);
   cudaFree(ws.staging);
   if (ws.h_ctrl) cudaFreeHost(ws.h_ctrl);
@@ -681,6 +684,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   A.heavy = ws.heavy;
   A.ctrl = ws.ctrl;
   A.heavy_min = p.ms_heavy_min;
+  A.order = p.ms_degree_order ? ws.order : nullptr;
   const int K = ws.ring;
   auto slot = [&](int l) { return ws.F + (long long)(l % K) * n * W; };
   // Unique sources form the level-0 frontier queue.

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_segmented_sort.cuh>
 
 #include "bfs_internal.cuh"
@@ -68,6 +69,55 @@ int reorder_impl(bfs_graph* g) {
 }
 
 }  // namespace
+
+namespace {
+
+template <typename RP>
+__global__ void k_degrees(const RP* rp, long long n, unsigned* deg, int* ids) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long v = tid; v < n; v += nth) {
+    const long long d = (long long)rp[v + 1] - (long long)rp[v];
+    deg[v] = d > 0xffffffffll ? 0xffffffffu : (unsigned)d;
+    ids[v] = (int)v;
+  }
+}
+
+template <typename RP>
+int degree_order_impl(bfs_graph* g, int* order) {
+  const long long n = g->n;
+  unsigned *k_in = nullptr, *k_out = nullptr;
+  int* ids = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  int rc = BFS_OK;
+  do {
+    cudaError_t e = cudaMalloc(&k_in, sizeof(unsigned) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&k_out, sizeof(unsigned) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&ids, sizeof(int) * (size_t)n);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc (degree order)", __FILE__, __LINE__); break; }
+    k_degrees<RP><<<g->num_sms * 8, 256>>>(reinterpret_cast<const RP*>(g->rp), n, k_in, ids);
+    e = cub::DeviceRadixSort::SortPairsDescending(nullptr, tmp_bytes, k_in, k_out, ids, order, (int)n);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes);
+    if (e == cudaSuccess) e = cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, k_in, k_out, ids, order, (int)n);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { rc = cuda_fail(e, "degree order sort", __FILE__, __LINE__); break; }
+  } while (0);
+  cudaFree(k_in);
+  cudaFree(k_out);
+  cudaFree(ids);
+  cudaFree(tmp);
+  return rc;
+}
+
+}  // namespace
+
+// Vertex ids ordered by degree, highest first (stable in id): the processing
+// order of multi-source pull levels, so that a warp's lanes scan lists of
+// similar length.
+int vertices_by_degree(bfs_graph* g, int* order) {
+  return g->rp_bits == 32 ? degree_order_impl<int>(g, order) : degree_order_impl<long long>(g, order);
+}
 
 int reorder_by_degree(bfs_graph* g) {
   return g->rp_bits == 32 ? reorder_impl<int>(g) : reorder_impl<long long>(g);

@@ -48,7 +48,8 @@ def test_rmat_group_sizes(bfs, bits, k):
 
 @pytest.mark.parametrize("kw", [dict(ms_lanes=64), dict(ms_lanes=7, ms_ring=2), dict(ms_heavy_min=0),
                                 dict(ms_heavy_min=1 << 30), dict(alpha=1, beta=1), dict(alpha=1000, beta=1000),
-                                dict(ms_ring=3, ms_lanes=130)])
+                                dict(ms_ring=3, ms_lanes=130), dict(ms_degree_order=1),
+                                dict(ms_degree_order=1, ms_heavy_min=0, ms_lanes=64)])
 def test_parameters(bfs, kw):
     rp, col = graphgen.rmat(12, seed=22)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_DEGREE_ORDER)
