@@ -234,6 +234,55 @@ int bfs_multi(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist
 int bfs_multi_ex(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist_bits,
                  const bfs_params *params, bfs_multi_stats *stats, void *stream);
 
+/* ---- graph sets: many small graphs, one source each, one launch ---- */
+
+typedef struct bfs_graphset bfs_graphset; /* opaque; owned by the library */
+
+/* Counters of one bfs_graphset_run. */
+typedef struct bfs_graphset_stats {
+    int32_t graphs;          /* graphs in the set */
+    int32_t max_levels;      /* largest eccentricity + 1 */
+    int32_t blocks;          /* persistent blocks launched */
+    int32_t pad;
+    int64_t levels;          /* levels processed, summed over graphs */
+    int64_t td_levels;       /* of which top-down */
+    int64_t bu_levels;       /* of which bottom-up */
+    int64_t reserved[4];
+} bfs_graphset_stats;
+
+/*
+ * Upload a set of `count` independent CSR graphs (host pointers), each with
+ * local vertex ids 0..n_i-1:
+ *  voff     int64[count+1]: graph i owns global vertex slots voff[i]..voff[i+1]-1
+ *           (n_i = voff[i+1] - voff[i] >= 1, n_i <= 2^19).
+ *  eoff     int64[count+1]: graph i's neighbour ids are col[eoff[i]..eoff[i+1]).
+ *  row_ptr  int64[voff[count] + count]: graph i's n_i+1 local row pointers start
+ *           at row_ptr[voff[i] + i] (each starts at 0).
+ *  col      int32[eoff[count]] local neighbour ids.
+ *  flags    BFS_VALIDATE checks every graph's CSR on the host.
+ * Every graph must be symmetric.  Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA.
+ */
+int bfs_graphset_upload(const int64_t *voff, const int64_t *eoff, const int64_t *row_ptr,
+                        const int32_t *col, int32_t count, int flags, bfs_graphset **out);
+
+/* Release a graph set (NULL is ignored). */
+void bfs_graphset_free(bfs_graphset *s);
+
+/*
+ * BFS of every graph of the set from its own source in ONE persistent launch
+ * (Section 2's hybrid BFS per graph, run inside one block with shared-memory
+ * bitmaps; blocks take graphs largest first).
+ *  srcs    host int32[count], local source id of each graph.
+ *  dist    int32[voff[count]] (device or host, detected): graph i's distances
+ *          at dist[voff[i] .. voff[i+1]), -1 = unreachable.
+ *  params  NULL = defaults (uses alpha, beta, threads_per_block <= 512,
+ *          blocks_per_sm).
+ *  stats   NULL or receives counters.
+ * Blocks until done.  Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA.
+ */
+int bfs_graphset_run(bfs_graphset *s, const int32_t *srcs, int32_t *dist, const bfs_params *params,
+                     bfs_graphset_stats *stats, void *stream);
+
 /*
  * bfs_single distances without any memory allocation (the paper has no
  * counterpart; this is a library-usage variant).

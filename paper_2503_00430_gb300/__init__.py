@@ -91,6 +91,17 @@ class bfs_multi_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class bfs_graphset_stats(ctypes.Structure):
+    _fields_ = [
+        ("graphs", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("blocks", ctypes.c_int32),
+        ("pad", ctypes.c_int32), ("levels", ctypes.c_int64), ("td_levels", ctypes.c_int64),
+        ("bu_levels", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "pad")}
+
+
 class bfs_level_stat(ctypes.Structure):
     _fields_ = [
         ("direction", ctypes.c_int32), ("converted", ctypes.c_int32), ("frontier", ctypes.c_int64),
@@ -121,6 +132,10 @@ _SIGNATURES = [
     ("bfs_multi", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, _vp]),
     ("bfs_multi_ex", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.POINTER(bfs_params),
                                     ctypes.POINTER(bfs_multi_stats), _vp]),
+    ("bfs_graphset_upload", ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, ctypes.c_int, ctypes.POINTER(_vp)]),
+    ("bfs_graphset_free", None, [_vp]),
+    ("bfs_graphset_run", ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(bfs_params),
+                                        ctypes.POINTER(bfs_graphset_stats), _vp]),
 ]
 
 
@@ -301,4 +316,49 @@ def bfs_multi_ex(g: Graph, srcs, dist, dist_bits: int = 32, params: bfs_params |
     _check(load().bfs_multi_ex(g.handle, _ptr(srcs), len(srcs), _ptr(dist), dist_bits,
                                ctypes.byref(params) if params is not None else None, ctypes.byref(st),
                                _stream_handle(stream)), "bfs_multi_ex")
+    return st.as_dict()
+
+
+class GraphSet:
+    """A set of small graphs resident on the device (``bfs_graphset*``)."""
+
+    def __init__(self, handle: int, count: int, total_v: int):
+        self.handle = handle
+        self.count = count
+        self.total_v = total_v
+
+    def free(self):
+        if self.handle:
+            load().bfs_graphset_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def bfs_graphset_upload(voff, eoff, row_ptr, col, flags: int = 0) -> GraphSet:
+    """Upload concatenated graphs (host numpy arrays; layout as in include/bfs.h)."""
+    voff = np.ascontiguousarray(voff, dtype=np.int64)
+    eoff = np.ascontiguousarray(eoff, dtype=np.int64)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().bfs_graphset_upload(_ptr(voff), _ptr(eoff), _ptr(row_ptr), _ptr(col) if len(col) else None,
+                                      len(voff) - 1, flags, ctypes.byref(h)), "bfs_graphset_upload")
+    return GraphSet(h.value, len(voff) - 1, int(voff[-1]))
+
+
+def bfs_graphset_free(s: GraphSet):
+    s.free()
+
+
+def bfs_graphset_run(s: GraphSet, srcs, dist, params: bfs_params | None = None, stream=None) -> dict:
+    """BFS of every graph from its source; distances into ``dist`` (int32[total vertices])."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.int32)
+    st = bfs_graphset_stats()
+    _check(load().bfs_graphset_run(s.handle, _ptr(srcs), _ptr(dist), ctypes.byref(params) if params is not None else None,
+                                   ctypes.byref(st), _stream_handle(stream)), "bfs_graphset_run")
     return st.as_dict()
