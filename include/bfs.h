@@ -283,6 +283,58 @@ void bfs_graphset_free(bfs_graphset *s);
 int bfs_graphset_run(bfs_graphset *s, const int32_t *srcs, int32_t *dist, const bfs_params *params,
                      bfs_graphset_stats *stats, void *stream);
 
+/* ---- serving: resident graphs, a stream of queries, continuous batching ---- */
+
+typedef struct bfs_server bfs_server; /* opaque; owned by the library */
+
+/* Timeline of one query (steady-clock nanoseconds). */
+typedef struct bfs_query_stats {
+    int64_t submit_ns;       /* bfs_serve_submit returned */
+    int64_t start_ns;        /* admitted into a lane */
+    int64_t done_ns;         /* result complete in the caller's buffer */
+    int32_t levels;          /* levels the query ran (its eccentricity + 1) */
+    int32_t lane;            /* lane it ran in */
+    int32_t graph_id;
+    int32_t status;          /* BFS_OK or an error code */
+    int64_t reserved[2];
+} bfs_query_stats;
+
+/*
+ * Start a server thread on the current device.  The server runs the queries
+ * of each registered graph in one 64-lane multi-source group (Section 2's
+ * level-synchronous loop for all lanes at once); a query waiting for a lane
+ * joins the running group at its next level and leaves when its frontier is
+ * empty, so queries overlap on the device as they arrive (continuous
+ * batching).  Admission is bounded by mem_budget bytes of device memory: a
+ * graph's group state (about (8*(2+ms_ring) + 16) bytes per vertex) when its
+ * first query arrives, and a 4n-byte staging buffer for every running query
+ * whose output is host memory.  Uses params->ms_ring, ms_heavy_min and tau_inv
+ * (levels run push when tau_inv * |F| < n, else pull).  NULL params = defaults.
+ */
+int bfs_serve_create(size_t mem_budget, const bfs_params *params, bfs_server **out);
+
+/* Register a graph (it stays owned by the caller and must outlive the server). */
+int bfs_serve_add_graph(bfs_server *srv, bfs_graph *g, int32_t *graph_id);
+
+/*
+ * Queue the query (graph_id, src).  dist_out: int32[n], device or host memory
+ * (detected; pinned host memory avoids a synchronous copy), owned by the caller
+ * and valid until the query is reported done.  Returns a ticket.
+ * Errors: BFS_EINVAL, BFS_ENOTFOUND (graph id), BFS_EAGAIN (queue full).
+ */
+int bfs_serve_submit(bfs_server *srv, int32_t graph_id, int32_t src, int32_t *dist_out, uint64_t *ticket);
+
+/* *done = 1 once the query's distances are complete.  A completed ticket is
+ * reported once (stats filled if non-NULL); later calls return BFS_ENOTFOUND. */
+int bfs_serve_poll(bfs_server *srv, uint64_t ticket, int *done, bfs_query_stats *stats);
+
+/* Block until the query completes (timeout_us < 0: no limit); then as poll.
+ * Returns BFS_ETIMEOUT if the limit passes first (the query keeps running). */
+int bfs_serve_wait(bfs_server *srv, uint64_t ticket, int64_t timeout_us, bfs_query_stats *stats);
+
+/* Finish running queries, drop queued ones, stop the thread, free the server. */
+void bfs_serve_destroy(bfs_server *srv);
+
 /*
  * bfs_single distances without any memory allocation (the paper has no
  * counterpart; this is a library-usage variant).

@@ -102,6 +102,17 @@ class bfs_graphset_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "pad")}
 
 
+class bfs_query_stats(ctypes.Structure):
+    _fields_ = [
+        ("submit_ns", ctypes.c_int64), ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+        ("levels", ctypes.c_int32), ("lane", ctypes.c_int32), ("graph_id", ctypes.c_int32),
+        ("status", ctypes.c_int32), ("reserved", ctypes.c_int64 * 2),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class bfs_level_stat(ctypes.Structure):
     _fields_ = [
         ("direction", ctypes.c_int32), ("converted", ctypes.c_int32), ("frontier", ctypes.c_int64),
@@ -136,6 +147,12 @@ _SIGNATURES = [
     ("bfs_graphset_free", None, [_vp]),
     ("bfs_graphset_run", ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(bfs_params),
                                         ctypes.POINTER(bfs_graphset_stats), _vp]),
+    ("bfs_serve_create", ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(bfs_params), ctypes.POINTER(_vp)]),
+    ("bfs_serve_add_graph", ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i32)]),
+    ("bfs_serve_submit", ctypes.c_int, [_vp, _i32, _i32, _vp, ctypes.POINTER(_u64)]),
+    ("bfs_serve_poll", ctypes.c_int, [_vp, _u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(bfs_query_stats)]),
+    ("bfs_serve_wait", ctypes.c_int, [_vp, _u64, _i64, ctypes.POINTER(bfs_query_stats)]),
+    ("bfs_serve_destroy", None, [_vp]),
 ]
 
 
@@ -362,3 +379,71 @@ def bfs_graphset_run(s: GraphSet, srcs, dist, params: bfs_params | None = None, 
     _check(load().bfs_graphset_run(s.handle, _ptr(srcs), _ptr(dist), ctypes.byref(params) if params is not None else None,
                                    ctypes.byref(st), _stream_handle(stream)), "bfs_graphset_run")
     return st.as_dict()
+
+
+class Server:
+    """A serving loop over resident graphs (``bfs_server*``)."""
+
+    def __init__(self, mem_budget: int, params: bfs_params | None = None):
+        h = ctypes.c_void_p()
+        _check(load().bfs_serve_create(int(mem_budget), ctypes.byref(params) if params is not None else None,
+                                       ctypes.byref(h)), "bfs_serve_create")
+        self.handle = h.value
+
+    def add_graph(self, g: Graph) -> int:
+        gid = ctypes.c_int32()
+        _check(load().bfs_serve_add_graph(self.handle, g.handle, ctypes.byref(gid)), "bfs_serve_add_graph")
+        return gid.value
+
+    def submit(self, graph_id: int, src: int, dist_out) -> int:
+        t = ctypes.c_uint64()
+        _check(load().bfs_serve_submit(self.handle, int(graph_id), int(src), _ptr(dist_out), ctypes.byref(t)),
+               "bfs_serve_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running, else the query's stats dict."""
+        done = ctypes.c_int()
+        st = bfs_query_stats()
+        _check(load().bfs_serve_poll(self.handle, ticket, ctypes.byref(done), ctypes.byref(st)), "bfs_serve_poll")
+        return st.as_dict() if done.value else None
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> dict:
+        st = bfs_query_stats()
+        _check(load().bfs_serve_wait(self.handle, ticket, int(timeout_us), ctypes.byref(st)), "bfs_serve_wait")
+        return st.as_dict()
+
+    def destroy(self):
+        if self.handle:
+            load().bfs_serve_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def bfs_serve_create(mem_budget: int, params: bfs_params | None = None) -> Server:
+    return Server(mem_budget, params)
+
+
+def bfs_serve_add_graph(srv: Server, g: Graph) -> int:
+    return srv.add_graph(g)
+
+
+def bfs_serve_submit(srv: Server, graph_id: int, src: int, dist_out) -> int:
+    return srv.submit(graph_id, src, dist_out)
+
+
+def bfs_serve_poll(srv: Server, ticket: int):
+    return srv.poll(ticket)
+
+
+def bfs_serve_wait(srv: Server, ticket: int, timeout_us: int = -1) -> dict:
+    return srv.wait(ticket, timeout_us)
+
+
+def bfs_serve_destroy(srv: Server):
+    srv.destroy()

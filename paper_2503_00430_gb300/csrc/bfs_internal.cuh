@@ -165,6 +165,17 @@ int ensure_multi_ws(bfs_graph* g, int ring);
 void free_multi_ws(bfs_graph* g);
 int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, const bfs_params& p,
               bfs_multi_stats* st, cudaStream_t s);
+// Serving groups (bfs_multi.cu): 64 lanes on one graph, lanes joining at level boundaries.
+struct ServeGroup;
+size_t serve_group_bytes(const bfs_graph* g, int ring);
+int serve_group_create(bfs_graph* g, int ring, int heavy_min, ServeGroup** out);
+void serve_group_destroy(ServeGroup* G);
+cudaStream_t serve_group_stream(ServeGroup* G);
+unsigned long long serve_group_lanes(const ServeGroup* G);
+int serve_group_level(const ServeGroup* G);
+int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* srcs, int* const* outs);
+int serve_group_launch(ServeGroup* G, int tau_inv);
+int serve_group_finish(ServeGroup* G, unsigned long long* retired);
 int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads_per_block,
                                cudaStream_t stream);
 

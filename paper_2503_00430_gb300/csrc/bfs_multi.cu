@@ -241,7 +241,8 @@ __global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
 
 // ---- apply after push: new lanes of touched vertices ----
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_apply(MsArgs A, long long nt) {
+__global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
+  const long long nt = (long long)A.ctrl->ntouch;  // written by k_ms_push earlier on this stream
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long nf = 0, mf = 0, dd = 0;
@@ -404,7 +405,9 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
 // (four gathers in flight per lane), stops once the vertex's pending active
 // lanes are all covered, and ORs the new lanes into the vertex's accumulator.
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_heavy_chunks(MsArgs A, long long nrec, long long nch) {
+__global__ void __launch_bounds__(256) k_ms_heavy_chunks(MsArgs A) {
+  const unsigned long long hv = A.ctrl->nheavy;  // written by k_ms_pull earlier on this stream
+  const long long nrec = (long long)(hv & ((1ull << kMsCountBits) - 1)), nch = (long long)(hv >> kMsCountBits);
   const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const unsigned lane = ms_lane();
@@ -475,7 +478,8 @@ __global__ void __launch_bounds__(256) k_ms_heavy_chunks(MsArgs A, long long nre
 
 // ---- apply the deferred vertices' accumulators ----
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_heavy_apply(MsArgs A, long long nrec) {
+__global__ void __launch_bounds__(256) k_ms_heavy_apply(MsArgs A) {
+  const long long nrec = (long long)(A.ctrl->nheavy & ((1ull << kMsCountBits) - 1));
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long nf = 0, mf = 0, dd = 0;
@@ -661,6 +665,23 @@ void free_multi_ws(bfs_graph* g) {
 
 namespace {
 
+// One level of a lane group, launched asynchronously: every count a later
+// kernel needs is read from the control block on the device.
+template <int W, typename RP>
+void ms_step(const MsArgs& A, bool push, long long nf, unsigned long long* Fn, long long n, int grid,
+             cudaStream_t s) {
+  cudaMemsetAsync(A.ctrl, 0, sizeof(MsCtrl), s);
+  if (push) {
+    k_ms_zero<<<grid, 256, 0, s>>>(Fn, n * W);
+    k_ms_push<W, RP><<<grid, 256, 0, s>>>(A, nf);
+    k_ms_apply<W, RP><<<grid, 256, 0, s>>>(A);
+  } else {
+    k_ms_pull<W, RP><<<grid, 256, 0, s>>>(A);
+    k_ms_heavy_chunks<W, RP><<<grid, 256, 0, s>>>(A);
+    k_ms_heavy_apply<W, RP><<<grid, 256, 0, s>>>(A);
+  }
+}
+
 template <int W, typename RP, typename T>
 int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, int max_level, const bfs_params& p,
               bfs_multi_stats* st, cudaStream_t s) {
@@ -732,33 +753,20 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
     A.Fnext = Fn;
     A.qcur = ws.q[qc];
     A.qnext = ws.q[qc ^ 1];
-    GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(MsCtrl), s));
-    if (push) {
-      k_ms_zero<<<grid, block, 0, s>>>(Fn, n * W);
-      k_ms_push<W, RP><<<grid, block, 0, s>>>(A, nf);
-      GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
-      GBFS_CUDA(cudaStreamSynchronize(s));
-      const long long nt = (long long)ws.h_ctrl->ntouch;
-      if (st) st->pushed_edges += (long long)ws.h_ctrl->edges;
-      if (nt > 0) k_ms_apply<W, RP><<<grid, block, 0, s>>>(A, nt);
-      if (st) ++st->push_levels;
-    } else {
-      k_ms_pull<W, RP><<<grid, block, 0, s>>>(A);
-      GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
-      GBFS_CUDA(cudaStreamSynchronize(s));
-      const unsigned long long hv = ws.h_ctrl->nheavy;
-      const long long nrec = (long long)(hv & ((1ull << kMsCountBits) - 1)), nch = (long long)(hv >> kMsCountBits);
-      if (nrec > 0) {
-        k_ms_heavy_chunks<W, RP><<<grid, block, 0, s>>>(A, nrec, nch);
-        k_ms_heavy_apply<W, RP><<<grid, block, 0, s>>>(A, nrec);
-      }
-      if (st) ++st->pull_levels;
-    }
+    ms_step<W, RP>(A, push, nf, Fn, n, grid, s);
     GBFS_CUDA(cudaGetLastError());
     GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
     GBFS_CUDA(cudaStreamSynchronize(s));
     const MsCtrl c = *ws.h_ctrl;
-    if (st && !push) st->pulled_edges += (long long)c.edges;
+    if (st) {
+      if (push) {
+        ++st->push_levels;
+        st->pushed_edges += (long long)c.edges;
+      } else {
+        ++st->pull_levels;
+        st->pulled_edges += (long long)c.edges;
+      }
+    }
     for (int k = 0; k < 4; ++k) A.act[k] = c.act[k];
     nf_prev = nf;
     nf = (long long)c.nf;
@@ -830,6 +838,330 @@ int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, co
   }
   GBFS_CUDA(cudaEventRecord(ws.done, s));
   GBFS_CUDA(cudaStreamSynchronize(s));
+  return BFS_OK;
+}
+
+}  // namespace gbfs
+
+// ============================================================================
+// Serving support: one 64-lane group per resident graph.  Queries join free
+// lanes at level boundaries (their own level 0 is the group's current level),
+// run with the other lanes, and leave when their frontier empties; their rows
+// are written from the frontier ring with per-lane offsets.
+// ============================================================================
+namespace gbfs {
+
+struct ServeGroup {
+  bfs_graph* g = nullptr;
+  int ring = 8;
+  long long n = 0;
+  int heavy_min = 256;
+  unsigned long long* X = nullptr;
+  unsigned long long* acc = nullptr;
+  unsigned long long* F = nullptr;
+  unsigned* touched_bm = nullptr;
+  int* q[2] = {nullptr, nullptr};
+  int* touched = nullptr;
+  MsHeavy* heavy = nullptr;
+  int* order = nullptr;
+  MsCtrl* ctrl = nullptr;
+  MsCtrl* h_ctrl = nullptr;
+  int** d_out = nullptr;   // [64] output row per lane
+  int* d_join = nullptr;   // [64] join level per lane
+  int* d_new = nullptr;    // [64] sources of joining lanes
+  int* d_newlane = nullptr;
+  int** h_out = nullptr;   // pinned mirrors
+  int* h_join = nullptr;
+  int* h_new = nullptr;
+  int* h_newlane = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_level = nullptr;
+  int L = 0, qc = 0, flushed = 0;
+  long long nf = 0;
+  unsigned long long lanes = 0, act = 0, first = 0;
+  bool launched = false;
+};
+
+namespace {
+
+__global__ void k_serve_clear(unsigned long long* X, long long n, unsigned long long keep) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long v = tid; v < n; v += nth) X[v] &= keep;
+}
+
+__global__ void k_serve_seed(unsigned long long* X, unsigned long long* Fcur, int* q, long long nf, const int* src,
+                             const int* lane, int count) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    const int s = src[k];
+    const unsigned long long bit = 1ull << lane[k];
+    atomicOr(X + s, bit);
+    atomicOr(Fcur + s, bit);
+    q[nf + k] = s;
+  }
+}
+
+// Rows of the lanes in `lanes` from ring levels [l0, l0+nlev): lane i's value
+// at a vertex is (level - join[i]) for the first level >= join[i] whose
+// frontier holds bit i (levels below join[i] are masked by valid[]), else -1
+// on the lane's first window.
+__global__ void __launch_bounds__(256) k_serve_write(const unsigned long long* F, long long n, int ring, int l0,
+                                                     int nlev, const unsigned long long* valid, unsigned long long lanes,
+                                                     unsigned long long first, int* const* out, const int* join) {
+  __shared__ unsigned long long pl[4][kWt];
+  __shared__ unsigned long long vmask[kMsMaxRing];
+  if (threadIdx.x < kMsMaxRing) vmask[threadIdx.x] = threadIdx.x < (unsigned)nlev ? valid[threadIdx.x] : 0ull;
+  const long long ntiles = (n + kWt - 1) / kWt;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __syncthreads();
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long v0 = tile * kWt;
+    for (int j = threadIdx.x; j < kWt; j += blockDim.x) {
+      const long long v = v0 + j;
+      unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0;
+      if (v < n) {
+        for (int l = nlev - 1; l >= 0; --l) {
+          const unsigned long long m = F[(long long)((l0 + l) % ring) * n + v] & vmask[l];
+          f |= m;
+          p0 = (p0 & ~m) | ((l & 1) ? m : 0ull);
+          p1 = (p1 & ~m) | ((l & 2) ? m : 0ull);
+          p2 = (p2 & ~m) | ((l & 4) ? m : 0ull);
+        }
+      }
+      pl[0][j] = f;
+      pl[1][j] = p0;
+      pl[2][j] = p1;
+      pl[3][j] = p2;
+    }
+    __syncthreads();
+    unsigned long long todo = lanes;
+    for (int r = 0; todo; ++r) {
+      const int i = __ffsll((long long)todo) - 1;
+      todo &= todo - 1;
+      if ((r % (int)nwarp) != (int)warp) continue;
+      const bool fst = (first >> i) & 1ull;
+      int* row = out[i] + v0;
+      const int jn = join[i];
+#pragma unroll
+      for (int q = 0; q < kWt / 32; ++q) {
+        const int j = (int)lane + 32 * q;
+        if (v0 + j >= n) break;
+        if ((pl[0][j] >> i) & 1ull) {
+          const int lv = (int)(((pl[1][j] >> i) & 1ull) | (((pl[2][j] >> i) & 1ull) << 1) |
+                               (((pl[3][j] >> i) & 1ull) << 2));
+          row[j] = l0 + lv - jn;
+        } else if (fst) {
+          row[j] = -1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename RP>
+void serve_step(ServeGroup* G, bool push) {
+  MsArgs A{};
+  A.rp = G->g->rp;
+  A.col = G->g->col;
+  A.n = G->n;
+  A.nw = G->g->nw;
+  A.full[0] = G->lanes;
+  A.act[0] = G->act;
+  for (int k = 1; k < 4; ++k) A.full[k] = A.act[k] = 0;
+  A.X = G->X;
+  A.acc = G->acc;
+  A.Fcur = G->F + (long long)(G->L % G->ring) * G->n;
+  A.Fnext = G->F + (long long)((G->L + 1) % G->ring) * G->n;
+  A.touched_bm = G->touched_bm;
+  A.qcur = G->q[G->qc];
+  A.qnext = G->q[G->qc ^ 1];
+  A.touched = G->touched;
+  A.heavy = G->heavy;
+  A.order = G->order;
+  A.ctrl = G->ctrl;
+  A.heavy_min = G->heavy_min;
+  ms_step<1, RP>(A, push, G->nf, A.Fnext, G->n, G->g->num_sms * 8, G->stream);
+}
+
+int serve_flush(ServeGroup* G, int upto) {
+  const int nlev = upto - G->flushed + 1;
+  if (nlev <= 0 || !G->lanes) {
+    G->flushed = upto + 1;
+    return BFS_OK;
+  }
+  unsigned long long valid[kMsMaxRing] = {0};
+  for (int l = 0; l < nlev; ++l)
+    for (int i = 0; i < 64; ++i)
+      if (((G->lanes >> i) & 1ull) && G->h_join[i] <= G->flushed + l) valid[l] |= 1ull << i;
+  unsigned long long* d_valid = reinterpret_cast<unsigned long long*>(G->ctrl + 1);
+  GBFS_CUDA(cudaMemcpyAsync(d_valid, valid, sizeof(valid), cudaMemcpyHostToDevice, G->stream));
+  k_serve_write<<<G->g->num_sms * 8, 256, 0, G->stream>>>(G->F, G->n, G->ring, G->flushed, nlev, d_valid, G->lanes,
+                                                           G->first, G->d_out, G->d_join);
+  GBFS_CUDA(cudaGetLastError());
+  G->first &= ~G->lanes;
+  G->flushed = upto + 1;
+  return BFS_OK;
+}
+
+}  // namespace
+
+size_t serve_group_bytes(const bfs_graph* g, int ring) {
+  const size_t n = (size_t)g->n;
+  const size_t heavy = (std::min(n, (size_t)g->m / 9) + 2) * sizeof(MsHeavy);
+  return n * 8 * (2 + (size_t)ring) + n * 4 * 4 + heavy + (size_t)g->nw * 4 + 4096;
+}
+
+int serve_group_create(bfs_graph* g, int ring, int heavy_min, ServeGroup** out) {
+  ServeGroup* G = new ServeGroup();
+  G->g = g;
+  G->ring = ring < 2 ? 2 : (ring > kMsMaxRing ? kMsMaxRing : ring);
+  G->n = g->n;
+  G->heavy_min = heavy_min;
+  const size_t n = (size_t)g->n;
+  int rc = BFS_OK;
+  do {
+    cudaError_t e = cudaMalloc(&G->X, 8 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&G->acc, 8 * n);
+    if (e == cudaSuccess) e = cudaMemset(G->acc, 0, 8 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&G->F, 8 * n * (size_t)G->ring);
+    if (e == cudaSuccess) e = cudaMalloc(&G->touched_bm, 4 * (size_t)g->nw);
+    if (e == cudaSuccess) e = cudaMemset(G->touched_bm, 0, 4 * (size_t)g->nw);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&G->q[i], 4 * n + 4 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&G->touched, 4 * n);
+    if (G->heavy_min < 8) G->heavy_min = 8;
+    const size_t heavy_cap = std::min(n, (size_t)g->m / (size_t)(G->heavy_min + 1)) + 2;
+    if (e == cudaSuccess) e = cudaMalloc(&G->heavy, sizeof(MsHeavy) * heavy_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&G->order, 4 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&G->ctrl, sizeof(MsCtrl) * 2);
+    if (e == cudaSuccess) e = cudaMallocHost(&G->h_ctrl, sizeof(MsCtrl));
+    if (e == cudaSuccess) e = cudaMalloc(&G->d_out, sizeof(int*) * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&G->d_join, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&G->d_new, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&G->d_newlane, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&G->h_out, sizeof(int*) * 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&G->h_join, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&G->h_new, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&G->h_newlane, sizeof(int) * 64);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->ev_level, cudaEventDisableTiming);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "serving group allocation", __FILE__, __LINE__); break; }
+    rc = vertices_by_degree(g, G->order);
+  } while (0);
+  if (rc != BFS_OK) {
+    serve_group_destroy(G);
+    return rc;
+  }
+  *out = G;
+  return BFS_OK;
+}
+
+void serve_group_destroy(ServeGroup* G) {
+  if (!G) return;
+  if (G->stream) cudaStreamSynchronize(G->stream);
+  cudaFree(G->X);
+  cudaFree(G->acc);
+  cudaFree(G->F);
+  cudaFree(G->touched_bm);
+  cudaFree(G->q[0]);
+  cudaFree(G->q[1]);
+  cudaFree(G->touched);
+  cudaFree(G->heavy);
+  cudaFree(G->order);
+  cudaFree(G->ctrl);
+  cudaFree(G->d_out);
+  cudaFree(G->d_join);
+  cudaFree(G->d_new);
+  cudaFree(G->d_newlane);
+  if (G->h_ctrl) cudaFreeHost(G->h_ctrl);
+  if (G->h_out) cudaFreeHost(G->h_out);
+  if (G->h_join) cudaFreeHost(G->h_join);
+  if (G->h_new) cudaFreeHost(G->h_new);
+  if (G->h_newlane) cudaFreeHost(G->h_newlane);
+  if (G->ev_level) cudaEventDestroy(G->ev_level);
+  if (G->stream) cudaStreamDestroy(G->stream);
+  delete G;
+}
+
+cudaStream_t serve_group_stream(ServeGroup* G) { return G->stream; }
+unsigned long long serve_group_lanes(const ServeGroup* G) { return G->lanes; }
+int serve_group_level(const ServeGroup* G) { return G->L; }
+
+int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* srcs, int* const* outs) {
+  if (count <= 0) return BFS_OK;
+  const int grid = G->g->num_sms * 8;
+  unsigned long long mask = 0;
+  for (int k = 0; k < count; ++k) mask |= 1ull << lanes_idx[k];
+  if (G->lanes == 0) {
+    // Idle group: start a new timeline at level 0.
+    G->L = 0;
+    G->qc = 0;
+    G->flushed = 0;
+    G->nf = 0;
+    G->act = 0;
+    k_ms_zero<<<grid, 256, 0, G->stream>>>(G->X, G->n);
+    k_ms_zero<<<grid, 256, 0, G->stream>>>(G->F, G->n);
+  } else {
+    k_serve_clear<<<grid, 256, 0, G->stream>>>(G->X, G->n, ~mask);
+  }
+  // A joining lane's level 0 is level L: it must lie in the next flushed window.
+  if (G->flushed > G->L) G->flushed = G->L;
+  for (int k = 0; k < count; ++k) {
+    G->h_new[k] = srcs[k];
+    G->h_newlane[k] = lanes_idx[k];
+    G->h_join[lanes_idx[k]] = G->L;
+    G->h_out[lanes_idx[k]] = outs[k];
+  }
+  GBFS_CUDA(cudaMemcpyAsync(G->d_new, G->h_new, sizeof(int) * (size_t)count, cudaMemcpyHostToDevice, G->stream));
+  GBFS_CUDA(cudaMemcpyAsync(G->d_newlane, G->h_newlane, sizeof(int) * (size_t)count, cudaMemcpyHostToDevice,
+                            G->stream));
+  GBFS_CUDA(cudaMemcpyAsync(G->d_join, G->h_join, sizeof(int) * 64, cudaMemcpyHostToDevice, G->stream));
+  GBFS_CUDA(cudaMemcpyAsync(G->d_out, G->h_out, sizeof(int*) * 64, cudaMemcpyHostToDevice, G->stream));
+  k_serve_seed<<<1, 64, 0, G->stream>>>(G->X, G->F + (long long)(G->L % G->ring) * G->n, G->q[G->qc], G->nf, G->d_new,
+                                        G->d_newlane, count);
+  GBFS_CUDA(cudaGetLastError());
+  G->nf += count;
+  G->lanes |= mask;
+  G->act |= mask;
+  G->first |= mask;
+  return BFS_OK;
+}
+
+int serve_group_launch(ServeGroup* G, int tau_inv) {
+  if (!G->lanes || G->launched) return BFS_OK;
+  if (G->L + 1 - G->flushed >= G->ring) {
+    const int rc = serve_flush(G, G->L);
+    if (rc != BFS_OK) return rc;
+  }
+  const bool push = (long long)tau_inv * G->nf < G->n;
+  if (G->g->rp_bits == 32) serve_step<int>(G, push); else serve_step<long long>(G, push);
+  GBFS_CUDA(cudaGetLastError());
+  GBFS_CUDA(cudaMemcpyAsync(G->h_ctrl, G->ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, G->stream));
+  GBFS_CUDA(cudaEventRecord(G->ev_level, G->stream));
+  G->launched = true;
+  return BFS_OK;
+}
+
+int serve_group_finish(ServeGroup* G, unsigned long long* retired) {
+  *retired = 0;
+  if (!G->launched) return BFS_OK;
+  GBFS_CUDA(cudaEventSynchronize(G->ev_level));
+  G->launched = false;
+  const MsCtrl c = *G->h_ctrl;
+  const unsigned long long act_next = c.act[0] & G->lanes;
+  const unsigned long long done = G->lanes & ~act_next;
+  G->nf = (long long)c.nf;
+  G->act = act_next;
+  if (done) {
+    // The finished lanes' last frontier is level L (their level L+1 is empty);
+    // level L+1 stays unflushed, so lanes that join there are written later.
+    const int rc = serve_flush(G, G->L);
+    if (rc != BFS_OK) return rc;
+    G->lanes &= ~done;
+  }
+  G->L += 1;
+  G->qc ^= 1;
+  *retired = done;
   return BFS_OK;
 }
 

@@ -1,0 +1,113 @@
+"""Serving loop: every query's distances equal the oracle's, alone or in a mix
+(bit-exact: the tolerance for serving is zero differences)."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bfs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_00430_gb300 as B
+    B.load()
+    return B
+
+
+@pytest.fixture(scope="module")
+def graphs(bfs):
+    gs = [graphgen.rmat(12, seed=31), graphgen.grid2d(40, 60), graphgen.erdos_renyi(3000, 10, 32),
+          G.csr_from_edges(50, [(i, i + 1) for i in range(20)])]
+    handles = [bfs.bfs_graph_upload(rp, col) for rp, col in gs]
+    yield gs, handles
+    for h in handles:
+        h.free()
+
+
+def run_mix(bfs, gs, handles, queries, budget=1 << 32, device_out=True, stagger=0.0, **kw):
+    srv = bfs.bfs_serve_create(budget, bfs.make_params(**kw) if kw else None)
+    ids = [srv.add_graph(h) for h in handles]
+    outs, tickets = [], []
+    for k, (gi, src) in enumerate(queries):
+        n = len(gs[gi][0]) - 1
+        out = (torch.full((n,), 77, dtype=torch.int32, device="cuda") if device_out
+               else torch.full((n,), 77, dtype=torch.int32).pin_memory().numpy() if k % 2 else np.full(n, 77, np.int32))
+        outs.append(out)
+        tickets.append(srv.submit(ids[gi], src, out))
+        if stagger:
+            time.sleep(stagger)
+    stats = [srv.wait(t, 60_000_000) for t in tickets]
+    for (gi, src), out in zip(queries, outs):
+        got = out.cpu().numpy() if hasattr(out, "cpu") else out
+        assert np.array_equal(got, oracle.bfs(*gs[gi], src)), (gi, src)
+    srv.destroy()
+    return stats
+
+
+def mix(gs, k, seed):
+    rng = np.random.default_rng(seed)
+    q = []
+    for _ in range(k):
+        gi = int(rng.integers(len(gs)))
+        q.append((gi, int(graphgen.sources(gs[gi][0], 1, int(rng.integers(1 << 30)))[0])))
+    return q
+
+
+def test_single_queries_alone(bfs, graphs):
+    gs, handles = graphs
+    for gi in range(len(gs)):
+        run_mix(bfs, gs, handles, [(gi, int(graphgen.sources(gs[gi][0], 1, 5)[0]))])
+
+
+def test_mix_many_queries_lane_reuse(bfs, graphs):
+    gs, handles = graphs
+    stats = run_mix(bfs, gs, handles, mix(gs, 300, 1))  # > 64 per graph: lanes are reused
+    assert all(s["status"] == 0 and s["done_ns"] >= s["start_ns"] >= s["submit_ns"] for s in stats)
+
+
+def test_staggered_arrivals_join_running_groups(bfs, graphs):
+    gs, handles = graphs
+    stats = run_mix(bfs, gs, handles, mix(gs, 120, 2), stagger=0.0005)
+    assert max(s["lane"] for s in stats) < 64
+
+
+def test_host_outputs_and_tight_budget(bfs, graphs):
+    gs, handles = graphs
+    # Budget: the groups plus only a few staging buffers, so host-output queries queue for memory.
+    run_mix(bfs, gs, handles, mix(gs, 40, 3), device_out=False, budget=80 << 20)
+
+
+@pytest.mark.parametrize("kw", [dict(ms_ring=2), dict(tau_inv=1), dict(tau_inv=100000), dict(ms_heavy_min=8)])
+def test_parameters(bfs, graphs, kw):
+    gs, handles = graphs
+    run_mix(bfs, gs, handles, mix(gs, 100, 4), **kw)
+
+
+def test_errors(bfs, graphs):
+    gs, handles = graphs
+    srv = bfs.bfs_serve_create(1 << 30)
+    gid = srv.add_graph(handles[3])
+    out = torch.empty(50, dtype=torch.int32, device="cuda")
+    with pytest.raises(bfs.BfsError) as e:
+        srv.submit(gid + 1, 0, out)
+    assert e.value.code == bfs.BFS_ENOTFOUND
+    with pytest.raises(bfs.BfsError) as e:
+        srv.submit(gid, 50, out)
+    assert e.value.code == bfs.BFS_EINVAL
+    t = srv.submit(gid, 3, out)
+    srv.wait(t)
+    with pytest.raises(bfs.BfsError) as e:
+        srv.poll(t)
+    assert e.value.code == bfs.BFS_ENOTFOUND
+    srv.destroy()
