@@ -79,6 +79,16 @@ def make_graph(scale):
     return rp, col, srcs
 
 
+def make_workload(args):
+    """(row_ptr, col, sources, row-pointer bytes, workload name) of the single-source workloads."""
+    import graphgen
+    if args.workload == "er24":
+        rp, col = graphgen.erdos_renyi(1 << 24, 16.0, 2)
+        return rp.astype(np.int32), col, graphgen.sources(rp, NSRC, SRC_SEED), 4, "er_2e24_d16_hybrid_64src"
+    rp, col, srcs = make_graph(args.scale)
+    return rp, col, srcs, 8, f"rmat_s{args.scale}_ef16_hybrid_64src"
+
+
 def harmonic_gteps(edges, seconds):
     """Harmonic mean of per-BFS rates edges_i / seconds_i, in 1e9 edges/s."""
     edges = np.asarray(edges, dtype=np.float64)
@@ -161,6 +171,8 @@ class ClockSampler:
 
 
 def cpu_baseline(rp, col, srcs, nsample):
+    if nsample <= 0:
+        return None
     """The oracle (serial queue BFS, one core) on a bounded sample of sources."""
     import oracle
     edges, secs = [], []
@@ -219,7 +231,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     t_gen = time.perf_counter()
-    rp, col, srcs = make_graph(args.scale)
+    rp, col, srcs, rp_bytes, wname = make_workload(args)
     t_gen = time.perf_counter() - t_gen
     n, m = len(rp) - 1, len(col)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER))
@@ -231,7 +243,7 @@ def run_ours(args):
     per_src = []
     for s in srcs:
         st, lv = bfs.bfs_single_ex(g, int(s), dist_buf, params=params, stats=True, level_cap=1 << 16, stream=stream)
-        per_src.append({"edges": st["edges_reached"] / 2, "bytes": algorithmic_bytes(n, 8, lv), "stats": st})
+        per_src.append({"edges": st["edges_reached"] / 2, "bytes": algorithmic_bytes(n, rp_bytes, lv), "stats": st})
 
     def one_step(times):
         for i, s in enumerate(srcs):
@@ -298,9 +310,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"rmat_s{args.scale}_ef16_hybrid_64src", "scale": args.scale,
-                   "edgefactor": EDGEFACTOR, "abcd": [0.57, 0.19, 0.19, 0.05], "n": n, "m": m,
-                   "row_ptr": "int64", "sources": len(srcs), "source_seed": SRC_SEED,
+        "config": {"workload": wname, "scale": args.scale if args.workload == "rmat25" else 24,
+                   "edgefactor": EDGEFACTOR, "abcd": [0.57, 0.19, 0.19, 0.05] if args.workload == "rmat25" else None,
+                   "n": n, "m": m, "row_ptr": "int64" if rp_bytes == 8 else "int32", "sources": len(srcs),
+                   "source_seed": SRC_SEED,
                    "policy": {0: "auto", 1: "frontier", 2: "edges", 3: "td_only"}.get(args.policy, str(args.policy)),
                    "launch": {0: "persistent", 1: "per_level", 2: "graph"}[args.launch],
                    "adjacency_order": "id" if args.no_degree_order else "degree_desc",
@@ -310,7 +323,8 @@ def run_ours(args):
         "latency": {"queries_per_s": len(secs) / float(np.sum(secs)), "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_kind": peak_kind, "traffic": measured_traffic() if args.scale == SCALE else None,
+                     "peak_kind": peak_kind,
+                     "traffic": measured_traffic() if (args.scale == SCALE and args.workload == "rmat25") else None,
                      "kernel": "bfs_persistent_kernel<long long,false> (one launch per BFS)",
                      "bytes_per_bfs_mean": float(np.mean([p["bytes"] for p in per_src]))},
         "e2e": e2e,
@@ -322,11 +336,270 @@ def run_ours(args):
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu
+    if args.workload != "rmat25":
+        out["metric"] = f"GTEPS (harmonic mean, 64 sources) {wname}"
     if rank == 0:
         print(json.dumps(out), flush=True)
     g.free()
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def _json(out):
+    print(json.dumps(out), flush=True)
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_large(args):
+    """Large-diameter graphs: 2-D grid 4096^2 and a random geometric graph of 2^23 points.
+
+    Per graph: 8 seeded sources; top-down only (the paper's large-diameter path,
+    Section 3) as one persistent launch, as a replayed CUDA graph of it, and as
+    one launch per level with the host reading the frontier size, to show what
+    the grid barrier saves.
+    """
+    import torch
+
+    import graphgen
+    import paper_2503_00430_gb300 as bfs
+    torch.cuda.set_device(0)
+    res = {}
+    for name, make in (("grid_4096x4096", lambda: graphgen.grid2d(4096, 4096)),
+                       ("rgg_2e23_d3", lambda: graphgen.rgg(1 << 23, graphgen.rgg_radius(1 << 23, 3.0), 3))):
+        rp, col = make()
+        srcs = graphgen.sources(rp, 8, 1003)
+        g = bfs.bfs_graph_upload(rp.astype(np.int32), col, flags=bfs.BFS_VALIDATE)
+        n = len(rp) - 1
+        d = torch.empty(n, dtype=torch.int32, device="cuda")
+        rec = {"n": n, "m": int(len(col))}
+        levels = []
+        for s_ in srcs:
+            st, _ = bfs.bfs_single_ex(g, int(s_), d, params=bfs.make_params(policy=3), stats=True)
+            levels.append(st["levels"])
+            reached = st["reached"]
+        rec["levels_mean"] = float(np.mean(levels))
+        rec["reached_last"] = int(reached)
+        for lname, launch in (("persistent", 0), ("graph", 2), ("per_level", 1)):
+            p = bfs.make_params(policy=3, launch=launch)
+            bfs.bfs_single_ex(g, int(srcs[0]), d, params=p)
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record()
+            t0 = time.perf_counter()
+            for s_ in srcs:
+                bfs.bfs_single_ex(g, int(s_), d, params=p)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / len(srcs)
+            rec[lname] = {"ms_per_bfs": ms, "us_per_level": 1e3 * ms / rec["levels_mean"],
+                          "wall_ms_per_bfs": 1e3 * (time.perf_counter() - t0) / len(srcs)}
+        rec["persistent_speedup_vs_per_level"] = rec["per_level"]["ms_per_bfs"] / rec["persistent"]["ms_per_bfs"]
+        res[name] = rec
+        g.free()
+    _json({"metric": "ms per BFS, large-diameter graphs (top-down only), persistent vs per-level launches",
+           "value": res["grid_4096x4096"]["persistent"]["ms_per_bfs"], "unit": "ms", "higher_is_better": False,
+           "n_gpus": 1, "dtype": "int32", "data": "synthetic", "config": {"workload": "large_diameter", **res}})
+    return 0
+
+
+def run_msbfs(args):
+    """Batched multi-source BFS: R-MAT scale 24, 256 sources per call, uint8 and int32 rows."""
+    import torch
+
+    import graphgen
+    import paper_2503_00430_gb300 as bfs
+    torch.cuda.set_device(0)
+    rp, col = graphgen.rmat(24, EDGEFACTOR, 0.57, 0.19, 0.19, 1, 1)
+    n = len(rp) - 1
+    srcs = graphgen.sources(rp, 256, 1004)
+    g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | bfs.BFS_DEGREE_ORDER)
+    d = torch.empty(n, dtype=torch.int32, device="cuda")
+    for s_ in srcs[:4]:
+        bfs.bfs_single(g, int(s_), d)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for s_ in srcs:
+        bfs.bfs_single(g, int(s_), d)
+    e1.record()
+    torch.cuda.synchronize()
+    single_s = e0.elapsed_time(e1) / 1e3 / len(srcs)
+    out = {"single_source_bfs_per_s": 1.0 / single_s}
+    for bits in (8, 32):
+        buf = torch.empty((256, n), dtype=torch.uint8 if bits == 8 else torch.int32, device="cuda")
+        st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        reps = max(1, args.steps // 4)
+        for _ in range(reps):
+            st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        out[f"uint{bits}" if bits == 8 else "int32"] = {"ms_per_call": t * 1e3, "bfs_per_s": 256 / t,
+                                                        "vs_single_source": 256 / t * single_s, "stats": st}
+        del buf
+    _json({"metric": "BFS/s, multi-source R-MAT s24 x 256 sources per call", "value": out["uint8"]["bfs_per_s"],
+           "unit": "BFS/s", "higher_is_better": True, "n_gpus": 1, "dtype": "u8", "data": "synthetic",
+           "config": {"workload": "msbfs_rmat_s24_256src", "n": n, "m": int(len(col)), **out}})
+    return 0
+
+
+def run_graphset(args):
+    """10,000 uniform random graphs, sizes log-uniform in [1e3, 1e5], mean degree 8, one launch."""
+    import torch
+
+    import graphgen
+    import paper_2503_00430_gb300 as bfs
+    torch.cuda.set_device(0)
+    count = args.graphs
+    gs = graphgen.graph_set(count, 1000, 100000, 8.0, seed=4)
+    s = bfs.bfs_graphset_upload(gs.voff, gs.eoff, gs.row_ptr, gs.col)
+    dist = torch.empty(int(gs.voff[-1]), dtype=torch.int32, device="cuda")
+    st = bfs.bfs_graphset_run(s, gs.src, dist)
+    torch.cuda.synchronize()
+    reps = max(3, args.steps)
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        st = bfs.bfs_graphset_run(s, gs.src, dist)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    # Sequential single-source baseline on a sample of the graphs (each uploaded on its own).
+    d = torch.empty(100000, dtype=torch.int32, device="cuda")
+    tot, k = 0.0, 0
+    for i in range(0, count, max(1, count // 100)):
+        rp, col = gs.graph(i)
+        g = bfs.bfs_graph_upload(rp, col)
+        bfs.bfs_single(g, int(gs.src[i]), d)
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        bfs.bfs_single(g, int(gs.src[i]), d)
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b) / 1e3
+        k += 1
+        g.free()
+    _json({"metric": "graphs/s, one launch over a set of small graphs", "value": count / t, "unit": "graphs/s",
+           "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": f"graphset_{count}_er_1e3_1e5_d8", "vertices": int(gs.voff[-1]),
+                      "entries": int(gs.eoff[-1]), "ms_per_launch": t * 1e3, "stats": st,
+                      "single_source_graphs_per_s": k / tot, "vs_single_source": (count / t) / (k / tot)}})
+    return 0
+
+
+def run_serve(args):
+    """Serving: five resident graphs, Poisson (graph, source) queries at offered
+    rates 0.1..0.9 and 1.2 x the measured capacity; queries/s and p50/p99
+    latency (arrival to result), against sequential single-source queries."""
+    import threading as th
+
+    import torch
+
+    import graphgen
+    import paper_2503_00430_gb300 as bfs
+    torch.cuda.set_device(0)
+    specs = [("rmat_s20", lambda: graphgen.rmat(20)), ("rmat_s22", lambda: graphgen.rmat(22)),
+             ("rmat_s24", lambda: graphgen.rmat(24)), ("grid_2048x2048", lambda: graphgen.grid2d(2048, 2048)),
+             ("er_2e22_d16", lambda: graphgen.erdos_renyi(1 << 22, 16.0, 5))]
+    graphs, handles, srcpool = [], [], []
+    for name, make in specs:
+        rp, col = make()
+        graphs.append((name, len(rp) - 1))
+        handles.append(bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_DEGREE_ORDER))
+        srcpool.append(graphgen.sources(rp, 4096, 1005))
+        del rp, col
+    rng = np.random.default_rng(5)
+
+    def draw(k):
+        gi = rng.integers(0, len(graphs), size=k)
+        return [(int(x), int(srcpool[x][rng.integers(0, 4096)])) for x in gi]
+
+    # Sequential single-source queries on the same mix.
+    d = {gi: torch.empty(graphs[gi][1], dtype=torch.int32, device="cuda") for gi in range(len(graphs))}
+    sample = draw(100)
+    for gi, sv in sample[:5]:
+        bfs.bfs_single(handles[gi], sv, d[gi])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for gi, sv in sample:
+        bfs.bfs_single(handles[gi], sv, d[gi])
+    torch.cuda.synchronize()
+    seq_qps = len(sample) / (time.perf_counter() - t0)
+
+    pool = 192  # output buffers per graph, recycled once their query is done
+    bufs = [[torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(pool)] for _, n in graphs]
+    srv = bfs.bfs_serve_create(200 << 30)
+    ids = [srv.add_graph(h) for h in handles]
+
+    def run_rate(rate, nq):
+        """Submit nq queries with Poisson arrivals at `rate` (inf = all at once); latencies in ms."""
+        qs = draw(nq)
+        arr = np.zeros(nq) if not np.isfinite(rate) else graphgen.poisson_arrivals(rate, nq, int(rng.integers(1 << 30)))
+        free = [list(range(pool)) for _ in graphs]
+        lock = th.Lock()
+        cv = th.Condition(lock)
+        tickets = [None] * nq
+        lat = np.zeros(nq)
+        t_arr = np.zeros(nq, dtype=np.int64)
+        done_evt = th.Event()
+
+        def waiter():
+            for i in range(nq):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                tk, gi, bi = tickets[i]
+                st = srv.wait(tk)
+                lat[i] = (st["done_ns"] - t_arr[i]) / 1e6
+                with cv:
+                    free[gi].append(bi)
+                    cv.notify_all()
+            done_evt.set()
+
+        w = th.Thread(target=waiter)
+        w.start()
+        start = time.monotonic_ns()
+        for i, (gi, sv) in enumerate(qs):
+            target = start + int(arr[i] * 1e9)
+            while True:
+                now = time.monotonic_ns()
+                if now >= target:
+                    break
+                if target - now > 200_000:
+                    time.sleep((target - now - 100_000) / 1e9)
+            with cv:
+                while not free[gi]:
+                    cv.wait()
+                bi = free[gi].pop()
+            t_arr[i] = max(target, start)
+            tickets[i] = (srv.submit(ids[gi], sv, bufs[gi][bi]), gi, bi)
+        done_evt.wait()
+        w.join()
+        wall = (time.monotonic_ns() - start) / 1e9
+        return {"offered_qps": None if not np.isfinite(rate) else rate, "queries": nq, "achieved_qps": nq / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean())}
+
+    run_rate(float("inf"), 256)  # warm-up: creates the groups
+    sat = run_rate(float("inf"), args.serve_queries)
+    cap = sat["achieved_qps"]
+    rates = {}
+    for f in (0.1, 0.3, 0.5, 0.7, 0.9, 1.2):
+        rates[str(f)] = run_rate(f * cap, args.serve_queries)
+    srv.destroy()
+    _json({"metric": "BFS queries/s & p99 latency, served mix of 5 resident graphs", "value": cap,
+           "unit": "queries/s", "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "serve_5graphs_poisson", "graphs": [g[0] for g in graphs],
+                      "saturated": sat, "sequential_single_source_qps": seq_qps, "vs_sequential": cap / seq_qps,
+                      "rates": rates}})
     return 0
 
 
@@ -343,12 +616,18 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-degree-order", action="store_true",
                     help="keep the generator's id-sorted adjacency order on the device")
+    ap.add_argument("--workload", default="rmat25",
+                    choices=["rmat25", "er24", "large", "msbfs", "graphset", "serve"])
+    ap.add_argument("--graphs", type=int, default=10000, help="graphset: graphs in the set")
+    ap.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per offered rate")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
-    return run_ours(args)
+    if args.workload in ("rmat25", "er24"):
+        return run_ours(args)
+    return {"large": run_large, "msbfs": run_msbfs, "graphset": run_graphset, "serve": run_serve}[args.workload](args)
 
 
 if __name__ == "__main__":

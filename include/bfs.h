@@ -234,6 +234,31 @@ int bfs_multi(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist
 int bfs_multi_ex(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist_bits,
                  const bfs_params *params, bfs_multi_stats *stats, void *stream);
 
+/* ---- autotuner ---- */
+
+/* Outcome of bfs_tune. */
+typedef struct bfs_tune_report {
+    int32_t trials;          /* parameter settings timed */
+    int32_t sources;         /* sample sources per trial */
+    double start_ms;         /* median BFS time with the starting parameters */
+    double best_ms;          /* median BFS time with the returned parameters */
+    int64_t reserved[4];
+} bfs_tune_report;
+
+/*
+ * Pick single-source parameters for graph g by coordinate descent: policy
+ * (Section 2's frontier rule, the edge-count rule, top-down only), alpha, beta,
+ * tau_inv, chunk, small_max, bu_thread_max, bu_warp_min, bu_chunk and
+ * threads_per_block are tried one field at a time (two sweeps); each setting is
+ * timed as the median over the k sample sources (CUDA events, after one warm
+ * run per source) and kept when it is at least 2% faster.  Every setting's
+ * distances must hash identically to the starting setting's; a mismatch
+ * aborts with BFS_ECUDA.  base = NULL starts from the defaults.
+ * Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ETIMEOUT.
+ */
+int bfs_tune(bfs_graph *g, const int32_t *srcs, int32_t k, const bfs_params *base, bfs_params *out,
+             bfs_tune_report *report);
+
 /* ---- graph sets: many small graphs, one source each, one launch ---- */
 
 typedef struct bfs_graphset bfs_graphset; /* opaque; owned by the library */

@@ -113,6 +113,16 @@ class bfs_query_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class bfs_tune_report(ctypes.Structure):
+    _fields_ = [
+        ("trials", ctypes.c_int32), ("sources", ctypes.c_int32), ("start_ms", ctypes.c_double),
+        ("best_ms", ctypes.c_double), ("reserved", ctypes.c_int64 * 4),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class bfs_level_stat(ctypes.Structure):
     _fields_ = [
         ("direction", ctypes.c_int32), ("converted", ctypes.c_int32), ("frontier", ctypes.c_int64),
@@ -147,6 +157,8 @@ _SIGNATURES = [
     ("bfs_graphset_free", None, [_vp]),
     ("bfs_graphset_run", ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(bfs_params),
                                         ctypes.POINTER(bfs_graphset_stats), _vp]),
+    ("bfs_tune", ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_params),
+                                ctypes.POINTER(bfs_tune_report)]),
     ("bfs_serve_create", ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(bfs_params), ctypes.POINTER(_vp)]),
     ("bfs_serve_add_graph", ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i32)]),
     ("bfs_serve_submit", ctypes.c_int, [_vp, _i32, _i32, _vp, ctypes.POINTER(_u64)]),
@@ -447,3 +459,57 @@ def bfs_serve_wait(srv: Server, ticket: int, timeout_us: int = -1) -> dict:
 
 def bfs_serve_destroy(srv: Server):
     srv.destroy()
+
+
+TUNABLE_FIELDS = ("policy", "alpha", "beta", "tau_inv", "chunk", "small_max", "bu_thread_max", "bu_warp_min",
+                  "bu_chunk", "threads_per_block")
+
+
+def params_to_dict(p: bfs_params) -> dict:
+    return {k: getattr(p, k) for k, _ in bfs_params._fields_ if k != "reserved"}
+
+
+def bfs_tune(g: Graph, srcs, base: bfs_params | None = None):
+    """Autotune single-source parameters on sample sources; returns (params, report dict)."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.int32)
+    out = bfs_params()
+    rep = bfs_tune_report()
+    _check(load().bfs_tune(g.handle, _ptr(srcs), len(srcs), ctypes.byref(base) if base is not None else None,
+                           ctypes.byref(out), ctypes.byref(rep)), "bfs_tune")
+    return out, rep.as_dict()
+
+
+def graph_class(n: int, m: int) -> str:
+    """Key of the tuning table: the paper's degree classes (Section 3: average degree below 7
+    is large-diameter) split further by size."""
+    avg = m / max(n, 1)
+    deg = "large_diameter" if avg < 7 else ("sparse" if avg < 24 else "dense")
+    return f"{deg}_n2e{max(0, int(np.log2(max(n, 1))))}"
+
+
+def tune_table_update(path: str, g: Graph, srcs) -> dict:
+    """Tune g and store the result under its graph class in a JSON table at ``path``."""
+    import json
+    params, rep = bfs_tune(g, srcs)
+    table = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            table = json.load(f)
+    key = graph_class(g.n, g.m)
+    table[key] = {"params": {k: getattr(params, k) for k in TUNABLE_FIELDS}, "report": rep}
+    with open(path, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    return table[key]
+
+
+def tuned_params(path: str, g: Graph) -> bfs_params:
+    """Defaults overridden by the table entry of g's class (defaults when absent)."""
+    import json
+    p = bfs_params_default()
+    if os.path.exists(path):
+        with open(path) as f:
+            entry = json.load(f).get(graph_class(g.n, g.m))
+        if entry:
+            for k, v in entry["params"].items():
+                setattr(p, k, v)
+    return p

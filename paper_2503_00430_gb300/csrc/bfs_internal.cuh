@@ -175,6 +175,7 @@ unsigned long long serve_group_lanes(const ServeGroup* G);
 int serve_group_level(const ServeGroup* G);
 int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* srcs, int* const* outs);
 int serve_group_launch(ServeGroup* G, int tau_inv);
+int serve_group_ready(ServeGroup* G);
 int serve_group_finish(ServeGroup* G, unsigned long long* retired);
 int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads_per_block,
                                cudaStream_t stream);

@@ -1142,6 +1142,14 @@ int serve_group_launch(ServeGroup* G, int tau_inv) {
   return BFS_OK;
 }
 
+// 1: a launched level has completed, 0: still running, -1: nothing launched.
+int serve_group_ready(ServeGroup* G) {
+  if (!G->launched) return -1;
+  const cudaError_t e = cudaEventQuery(G->ev_level);
+  if (e == cudaErrorNotReady) return 0;
+  return 1;  // errors surface in serve_group_finish's synchronize
+}
+
 int serve_group_finish(ServeGroup* G, unsigned long long* retired) {
   *retired = 0;
   if (!G->launched) return BFS_OK;

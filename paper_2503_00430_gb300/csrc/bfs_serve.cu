@@ -7,9 +7,10 @@
 // needs a free lane and, if its output is host memory, a device staging
 // buffer of 4n bytes within the budget - where they join the running group at
 // its next level, (3) launches one level of every busy group (each on its own
-// stream, so groups on different graphs overlap on the GPU), (4) waits for the
-// levels and retires lanes whose frontier emptied: their rows are written and,
-// for host outputs, copied back; a query is done when its copy has finished.
+// stream, so groups on different graphs overlap on the GPU); each group moves
+// on to its next level as soon as its own level has finished (groups are not
+// in lockstep), retiring lanes whose frontier emptied: their rows are written
+// and, for host outputs, copied back; a query is done when its copy is.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -105,8 +106,35 @@ bool server_pass(bfs_server* S) {
     admit = !S->stop;
   }
   bool busy = false;
-  // Admission and launch.
   for (GraphEntry* ge : ges) {
+    // A group advances as soon as its own level is done, independently of the others.
+    if (ge->grp) {
+      const int r = gbfs::serve_group_ready(ge->grp);
+      if (r == 0) {
+        busy = true;
+        continue;
+      }
+      if (r == 1) {
+        unsigned long long retired = 0;
+        const int rc = gbfs::serve_group_finish(ge->grp, &retired);
+        if (rc != BFS_OK) S->error = rc;
+        while (retired) {
+          const int i = __builtin_ctzll(retired);
+          retired &= retired - 1;
+          Query* q = ge->lane_q[i];
+          ge->lane_q[i] = nullptr;
+          if (!q) continue;
+          q->levels = gbfs::serve_group_level(ge->grp) - q->join;
+          cudaStream_t st = gbfs::serve_group_stream(ge->grp);
+          if (q->host_out)
+            cudaMemcpyAsync(q->user_out, q->dev_out, sizeof(int32_t) * (size_t)ge->g->n, cudaMemcpyDeviceToHost, st);
+          cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
+          cudaEventRecord(q->ev, st);
+          S->completing.push_back(q);
+        }
+      }
+    }
+    // Admission into free lanes, then the next level.
     const unsigned long long in_use = ge->grp ? gbfs::serve_group_lanes(ge->grp) : 0ull;
     std::vector<int> lanes, srcs;
     std::vector<int*> outs;
@@ -170,27 +198,6 @@ bool server_pass(bfs_server* S) {
     }
     if (admit && !ge->pending.empty()) busy = true;
   }
-  // Finish the launched levels; retire lanes whose search ended.
-  for (GraphEntry* ge : ges) {
-    if (!ge->grp) continue;
-    unsigned long long retired = 0;
-    const int rc = gbfs::serve_group_finish(ge->grp, &retired);
-    if (rc != BFS_OK) S->error = rc;
-    while (retired) {
-      const int i = __builtin_ctzll(retired);
-      retired &= retired - 1;
-      Query* q = ge->lane_q[i];
-      ge->lane_q[i] = nullptr;
-      if (!q) continue;
-      q->levels = gbfs::serve_group_level(ge->grp) - q->join;
-      cudaStream_t st = gbfs::serve_group_stream(ge->grp);
-      if (q->host_out)
-        cudaMemcpyAsync(q->user_out, q->dev_out, sizeof(int32_t) * (size_t)ge->g->n, cudaMemcpyDeviceToHost, st);
-      cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
-      cudaEventRecord(q->ev, st);
-      S->completing.push_back(q);
-    }
-  }
   // Completions.
   std::vector<Query*> still;
   for (Query* q : S->completing) {
@@ -221,6 +228,10 @@ void server_main(bfs_server* S) {
     std::unique_lock<std::mutex> lk(S->mu);
     if (S->stop && !busy && S->inbox.empty()) break;
     if (!busy && S->inbox.empty()) S->cv_work.wait_for(lk, std::chrono::milliseconds(1));
+    else if (busy) {
+      lk.unlock();
+      std::this_thread::yield();
+    }
   }
 }
 

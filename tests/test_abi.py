@@ -58,3 +58,10 @@ def test_host_only_calls_fail_cleanly_without_gpu(lib_path):
         B.bfs_graph_upload(np.array([0, 0], dtype=np.int64), np.zeros(0, dtype=np.int32), n=0)
     assert e.value.code == B.BFS_EINVAL
 
+
+
+def test_graph_class_keys():
+    import paper_2503_00430_gb300 as B
+    assert B.graph_class(4096 * 4096, 67092480).startswith("large_diameter")
+    assert B.graph_class(1 << 25, 1047207640) == "dense_n2e25"
+    assert B.graph_class(1 << 24, 268435294) == "sparse_n2e24"
