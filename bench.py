@@ -89,6 +89,24 @@ def make_workload(args):
     return rp, col, srcs, 8, f"rmat_s{args.scale}_ef16_hybrid_64src"
 
 
+def aggregate_ranks(total_ms, value, device="cuda"):
+    """Max of the timed region over ranks and the sum of the per-rank rates
+    (independent replicas: the job's throughput is the sum)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, value], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
+def replica_sources(srcs, rank, world):
+    """Sources a rank runs: replicas each run the whole workload (weak scaling)."""
+    return list(srcs)
+
+
 def harmonic_gteps(edges, seconds):
     """Harmonic mean of per-BFS rates edges_i / seconds_i, in 1e9 edges/s."""
     edges = np.asarray(edges, dtype=np.float64)
@@ -232,6 +250,7 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     t_gen = time.perf_counter()
     rp, col, srcs, rp_bytes, wname = make_workload(args)
+    srcs = np.asarray(replica_sources(srcs, rank, world), dtype=np.int32)
     t_gen = time.perf_counter() - t_gen
     n, m = len(rp) - 1, len(col)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER))
@@ -278,13 +297,7 @@ def run_ours(args):
     byts = [per_src[i]["bytes"] for i, _, _ in recs]
     value = harmonic_gteps(edges, secs)
     if world > 1:
-        t = torch.tensor([total_ms, value], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        total_ms = float(mx[0])
-        value = float(sm[1])
+        total_ms, value = aggregate_ranks(total_ms, value)
     lat = np.array(secs) * 1e3
     hbm, peak_kind = peaks()
     achieved = float(np.sum(byts) / np.sum(secs) / 1e9)
