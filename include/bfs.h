@@ -54,6 +54,12 @@ extern "C" {
 #define BFS_DEGREE_ORDER 8     /* store each adjacency list highest-degree neighbour first (ties by
                                   id); distances are unchanged, bottom-up scans stop sooner.
                                   Needs m < 2^31 and temporary device memory of 16*m bytes. */
+#define BFS_NO_HEAD 16         /* do not build the per-vertex head table.  By default (when m < 2^31)
+                                  the upload stores, for every vertex, its first two neighbours, the
+                                  start of its list and its degree (16 bytes per vertex, after any
+                                  degree ordering), so that a bottom-up probe of the first neighbours
+                                  and a top-down degree lookup read one record instead of row_ptr and
+                                  col_idx.  Distances are unchanged either way. */
 
 /* ---- direction policies (bfs_params.policy) ----
  * Every policy yields the same distances; they differ only in work.

@@ -34,6 +34,7 @@ BFS_DEVICE_PTRS = 1
 BFS_VALIDATE = 2
 BFS_VALIDATE_SYMMETRY = 4
 BFS_DEGREE_ORDER = 8
+BFS_NO_HEAD = 16
 
 BFS_POLICY_AUTO = 0
 BFS_POLICY_FRONTIER = 1

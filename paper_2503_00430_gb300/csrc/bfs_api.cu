@@ -163,10 +163,38 @@ void release_graph(bfs_graph* g) {
   if (g->rp) cudaFree(g->rp);
   if (g->col) cudaFree(g->col);
   if (g->init_vis) cudaFree(g->init_vis);
+  if (g->head) cudaFree(g->head);
   delete g;
 }
 
+// head[v] = {col[s] or -1, col[s+1] or -1, s, degree} with s = rp[v].
+template <typename RP>
+__global__ void k_build_head(const RP* rp, const int* col, long long n, int4* head) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long v = tid; v < n; v += nth) {
+    const long long s = (long long)rp[v];
+    const long long d = (long long)rp[v + 1] - s;
+    head[v] = make_int4(d > 0 ? col[s] : -1, d > 1 ? col[s + 1] : -1, (int)s, (int)d);
+  }
+}
+
 }  // namespace
+
+// The per-vertex head table (built after any reordering of the lists).  List
+// starts are stored as int32, so graphs with m >= 2^31 get none.
+int build_head(bfs_graph* g) {
+  if (g->m >= ((long long)1 << 31) - 8) return BFS_OK;
+  GBFS_CUDA(cudaMalloc(&g->head, sizeof(int4) * (size_t)g->n));
+  const int grid = g->num_sms * 4, block = 256;
+  if (g->rp_bits == 32)
+    k_build_head<int><<<grid, block>>>(static_cast<const int*>(g->rp), g->col, g->n, g->head);
+  else
+    k_build_head<long long><<<grid, block>>>(static_cast<const long long*>(g->rp), g->col, g->n, g->head);
+  GBFS_CUDA(cudaGetLastError());
+  GBFS_CUDA(cudaDeviceSynchronize());
+  return BFS_OK;
+}
 
 int ensure_single_ws(bfs_graph* g) {
   SingleWs& ws = g->ws;
@@ -308,6 +336,7 @@ int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_i
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy (graph)", __FILE__, __LINE__); break; }
     rc = row_ptr_bits == 32 ? validate_and_facts<int>(g, flags) : validate_and_facts<long long>(g, flags);
     if (rc == BFS_OK && (flags & BFS_DEGREE_ORDER)) rc = reorder_by_degree(g);
+    if (rc == BFS_OK && !(flags & BFS_NO_HEAD)) rc = build_head(g);
   } while (0);
   if (rc != BFS_OK) {
     release_graph(g);

@@ -50,6 +50,9 @@ struct KParams {
   int nw;                    // bitmap words = ceil(n / 32)
   int src;
   const unsigned* init_vis;  // degree-0 vertices and padding bits set
+  const int4* head;          // per vertex {first neighbour, second neighbour, list start, degree}
+                             // (-1 for a missing neighbour), or null: read rp / col instead
+  long long n_live;          // vertices of degree > 0 (n when unknown)
   int* dist;
   unsigned* vis;
   unsigned* bm0;
@@ -139,6 +142,7 @@ struct bfs_graph {
   void* rp = nullptr;         // device row pointers
   int* col = nullptr;         // device neighbour ids (padded)
   unsigned* init_vis = nullptr;
+  int4* head = nullptr;       // per-vertex head table (null with BFS_NO_HEAD or m >= 2^31)
   long long max_deg = 0, isolated = 0;
   std::mutex mu;
   gbfs::SingleWs ws;
@@ -156,6 +160,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
 bool is_device_pointer(const void* p);
 int reorder_by_degree(bfs_graph* g);
+int build_head(bfs_graph* g);
 int vertices_by_degree(bfs_graph* g, int* order);
 int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);

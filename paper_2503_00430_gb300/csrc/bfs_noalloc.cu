@@ -130,6 +130,8 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   K.nw = (int)((n + 31) / 32);
   K.src = src;
   K.init_vis = reinterpret_cast<unsigned*>(b + lay.init_vis);
+  K.head = nullptr;
+  K.n_live = n;
   K.dist = dist;
   K.vis = reinterpret_cast<unsigned*>(b + lay.vis);
   K.bm0 = reinterpret_cast<unsigned*>(b + lay.bm0);

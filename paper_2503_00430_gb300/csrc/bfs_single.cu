@@ -66,6 +66,14 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Asynchronous 16-byte global -> shared copy (zero-filled when src_bytes is 0).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <typename RP>
 __device__ __forceinline__ long long rp_at(const void* rp, long long i) {
   return (long long)__ldg(reinterpret_cast<const RP*>(rp) + i);
@@ -306,8 +314,14 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, const int (&c
     d[k] = 0;
     if ((cl >> k) & 1u) {
       P.dist[c[k]] = L + 1;
-      s[k] = rp_at<RP>(P.rp, c[k]);
-      d[k] = (int)(rp_at<RP>(P.rp, (long long)c[k] + 1) - s[k]);
+      if (P.head) {
+        const int4 h = __ldg(P.head + c[k]);
+        s[k] = h.z;
+        d[k] = h.w;
+      } else {
+        s[k] = rp_at<RP>(P.rp, c[k]);
+        d[k] = (int)(rp_at<RP>(P.rp, (long long)c[k] + 1) - s[k]);
+      }
     }
   }
   const int ncl = __popc(cl);
@@ -479,9 +493,14 @@ __device__ __forceinline__ bool in_frontier(const unsigned* front, int u) {
 #ifndef GBFS_BU_U
 #define GBFS_BU_U 2
 #endif
+#ifndef GBFS_DRAIN_MIN
+#define GBFS_DRAIN_MIN 32
+#endif
 constexpr int kBuU = GBFS_BU_U;       // unvisited vertices per lane in flight in a bottom-up round
-constexpr int kPendCap = 32 * kBuU;   // deferred long scans per warp (one round's worth)
+constexpr int kDrainMin = GBFS_DRAIN_MIN;  // deferred scans that trigger a drain within a batch
+constexpr int kPendCap = 32 * kBuU + kDrainMin - 1;  // deferred long scans per warp
 struct BuWarpSmem {
+  int4 hbuf[2][32 * kBuU];       // head records of the current and the next round (lane-private slots)
   unsigned next[32];             // new-frontier bits of the batch's 32 words
   long long pstart[kPendCap];    // deferred scan: next entry to examine
   int plen[kPendCap];            // entries left
@@ -512,34 +531,38 @@ __device__ void bu_drain(const KParams& P, int L, const unsigned* front, BuWarpS
   for (int g0 = 0; g0 < np; g0 += 32) {
     const int j = g0 + (int)lane;
     const bool have = j < np;
-    long long ps = have ? sm.pstart[j] : 0;  // 4-aligned
+    long long ps = have ? sm.pstart[j] : 0;
     int pl = have ? sm.plen[j] : 0;
     const int pv = have ? sm.pv[j] : 0;
     const int pdeg = have ? sm.pd[j] : 0;
     int ex = have ? sm.pex[j] : 0;
     // Each lane first continues its own vertex for up to bu_thread_max entries,
-    // one aligned 128-bit group (four probes in flight) at a time.
+    // one aligned 128-bit group (up to four probes in flight) at a time; the
+    // first group masks the entries before ps.
     bool tfound = false;
-    for (int done = 0; pl > 0 && done < P.bu_thread_max; done += 4) {
-      const int4 q = __ldg(reinterpret_cast<const int4*>(P.col + ps));
+    for (int done = 0; pl > 0 && done < P.bu_thread_max;) {
+      const long long a = ps & ~3ll;
+      const int off = (int)(ps - a);
+      const int4 q = __ldg(reinterpret_cast<const int4*>(P.col + a));
       const int c4[4] = {q.x, q.y, q.z, q.w};
       bool h[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) h[t] = t < pl && ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u);
+      for (int t = 0; t < 4; ++t) h[t] = t >= off && t - off < pl && ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u);
       int ft = -1;
 #pragma unroll
       for (int t = 3; t >= 0; --t)
         if (h[t]) ft = t;
       if (ft >= 0) {
         tfound = true;
-        ex += ft + 1;
+        ex += ft - off + 1;
         pl = 0;
         break;
       }
-      const int step = pl < 4 ? pl : 4;
+      const int step = pl < 4 - off ? pl : 4 - off;
       ex += step;
       pl -= step;
-      ps += 4;
+      ps += step;
+      done += step;
     }
     const bool heavy = pl > P.bu_warp_min;
     const int len = heavy ? 0 : pl;
@@ -623,6 +646,23 @@ __device__ void bu_drain(const KParams& P, int L, const unsigned* front, BuWarpS
   __syncwarp();
 }
 
+// Warp-collective: the unvisited vertices r0 + 32k + lane (k < kBuU) of a batch
+// whose 32 words have active masks `act` (one per lane) and exclusive prefix
+// counts `excl`; -1 past the end.
+__device__ __forceinline__ void round_vertices(unsigned act, int excl, int total, long long w0, int r0,
+                                               int (&v)[kBuU]) {
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int k = 0; k < kBuU; ++k) {
+    const int kk = r0 + 32 * k + (int)lane;
+    const int wo = owner_of(excl, kk);
+    const unsigned aw = __shfl_sync(kFull, act, wo);
+    const int ew = __shfl_sync(kFull, excl, wo);
+    v[k] = -1;
+    if (kk < total) v[k] = (int)((w0 + wo) * 32 + (long long)nth_set_bit(aw, kk - ew));
+  }
+}
+
 // One batch of 32 bitmap words (1024 vertices) of a bottom-up level, by one
 // warp.  The unvisited vertices of the batch are packed onto the lanes, two
 // per lane at a time; each looks for a frontier neighbour among the first
@@ -644,70 +684,116 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
   const int total = __shfl_sync(kFull, incl, 31);
   if (STATS) acc.unvisited += (unsigned long long)cnt;
   __syncwarp();
-  for (int r0 = 0; r0 < total; r0 += 32 * kBuU) {
+  int vn[kBuU];
+  if (P.head && total > 0) {
+    // Prologue of the head pipeline: round 0's records are requested now.
+    round_vertices(act, excl, total, w0, 0, vn);
+#pragma unroll
+    for (int k = 0; k < kBuU; ++k)
+      cp_async16(&sm.hbuf[0][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
+    cp_async_commit();
+  }
+  for (int r0 = 0, buf = 0; r0 < total; r0 += 32 * kBuU, buf ^= 1) {
     int v[kBuU];
-    long long s[kBuU], e[kBuU];
+    if (P.head) {
+      // Head table: the first two neighbours (highest degree first under
+      // degree ordering), the list start and the degree in one 16-byte record.
+      // The next round's records are requested before this round's are used,
+      // so a warp keeps one round of head loads in flight while it probes,
+      // marks and drains.  Each lane reads only the slots it filled itself.
 #pragma unroll
-    for (int k = 0; k < kBuU; ++k) {
-      const int kk = r0 + 32 * k + (int)lane;
-      const int wo = owner_of(excl, kk);
-      const unsigned aw = __shfl_sync(kFull, act, wo);
-      const int ew = __shfl_sync(kFull, excl, wo);
-      v[k] = -1;
-      if (kk < total) v[k] = (int)((w0 + wo) * 32 + (long long)nth_set_bit(aw, kk - ew));
-    }
+      for (int k = 0; k < kBuU; ++k) v[k] = vn[k];
+      if (r0 + 32 * kBuU < total) {
+        round_vertices(act, excl, total, w0, r0 + 32 * kBuU, vn);
 #pragma unroll
-    for (int k = 0; k < kBuU; ++k) {
-      s[k] = 0;
-      e[k] = 0;
-      if (v[k] >= 0) {
-        s[k] = rp_at<RP>(P.rp, v[k]);
-        e[k] = rp_at<RP>(P.rp, (long long)v[k] + 1);
+        for (int k = 0; k < kBuU; ++k)
+          cp_async16(&sm.hbuf[buf ^ 1][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
       }
-    }
-    int4 q[kBuU];
+      cp_async_commit();
+      cp_async_wait1();
+      int4 hd[kBuU];
 #pragma unroll
-    for (int k = 0; k < kBuU; ++k) {
-      q[k] = make_int4(0, 0, 0, 0);
-      if (e[k] > s[k]) q[k] = __ldg(reinterpret_cast<const int4*>(P.col + (s[k] & ~3ll)));
-    }
-    unsigned f[kBuU][4];
+      for (int k = 0; k < kBuU; ++k) hd[k] = v[k] >= 0 ? sm.hbuf[buf][32 * k + lane] : make_int4(-1, -1, 0, 0);
+      unsigned f0[kBuU], f1[kBuU];
 #pragma unroll
-    for (int k = 0; k < kBuU; ++k) {
-      const long long a0 = s[k] & ~3ll;
-      const int c4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const bool ok = a0 + t >= s[k] && a0 + t < e[k];
-        f[k][t] = ok ? ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u) : 0u;
+      for (int k = 0; k < kBuU; ++k) {
+        f0[k] = hd[k].x >= 0 ? ((front[hd[k].x >> 5] >> (hd[k].x & 31)) & 1u) : 0u;
+        f1[k] = hd[k].y >= 0 ? ((front[hd[k].y >> 5] >> (hd[k].y & 31)) & 1u) : 0u;
       }
-    }
 #pragma unroll
-    for (int k = 0; k < kBuU; ++k) {
-      if (v[k] < 0) continue;
-      const long long a0 = s[k] & ~3ll;
-      long long hit = -1;
+      for (int k = 0; k < kBuU; ++k) {
+        if (v[k] < 0) continue;
+        const int d = hd[k].w;
+        if (f0[k] | f1[k]) {
+          bu_mark_found(P, L, sm, w0, v[k], d, acc);
+          if (STATS) acc.edges += f0[k] ? 1ull : 2ull;
+        } else if (d > 2) {
+          const int slot = atomicAdd(&sm.npend, 1);
+          sm.pstart[slot] = (long long)hd[k].z + 2;
+          sm.plen[slot] = d - 2;
+          sm.pv[slot] = v[k];
+          sm.pd[slot] = d;
+          sm.pex[slot] = 2;
+        } else if (STATS) {
+          acc.edges += (unsigned long long)d;
+        }
+      }
+    } else {
+      round_vertices(act, excl, total, w0, r0, v);
+      long long s[kBuU], e[kBuU];
 #pragma unroll
-      for (int t = 3; t >= 0; --t)
-        if (f[k][t]) hit = a0 + t;
-      const int d = (int)(e[k] - s[k]);
-      const long long rest = a0 + 4;
-      if (hit >= 0) {
-        bu_mark_found(P, L, sm, w0, v[k], d, acc);
-        if (STATS) acc.edges += (unsigned long long)(hit - s[k] + 1);
-      } else if (rest < e[k]) {
-        const int slot = atomicAdd(&sm.npend, 1);
-        sm.pstart[slot] = rest;
-        sm.plen[slot] = (int)(e[k] - rest);
-        sm.pv[slot] = v[k];
-        sm.pd[slot] = d;
-        sm.pex[slot] = (int)(rest - s[k]);
-      } else if (STATS) {
-        acc.edges += (unsigned long long)d;
+      for (int k = 0; k < kBuU; ++k) {
+        s[k] = 0;
+        e[k] = 0;
+        if (v[k] >= 0) {
+          s[k] = rp_at<RP>(P.rp, v[k]);
+          e[k] = rp_at<RP>(P.rp, (long long)v[k] + 1);
+        }
+      }
+      int4 q[kBuU];
+#pragma unroll
+      for (int k = 0; k < kBuU; ++k) {
+        q[k] = make_int4(0, 0, 0, 0);
+        if (e[k] > s[k]) q[k] = __ldg(reinterpret_cast<const int4*>(P.col + (s[k] & ~3ll)));
+      }
+      unsigned f[kBuU][4];
+#pragma unroll
+      for (int k = 0; k < kBuU; ++k) {
+        const long long a0 = s[k] & ~3ll;
+        const int c4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const bool ok = a0 + t >= s[k] && a0 + t < e[k];
+          f[k][t] = ok ? ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u) : 0u;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kBuU; ++k) {
+        if (v[k] < 0) continue;
+        const long long a0 = s[k] & ~3ll;
+        long long hit = -1;
+#pragma unroll
+        for (int t = 3; t >= 0; --t)
+          if (f[k][t]) hit = a0 + t;
+        const int d = (int)(e[k] - s[k]);
+        const long long rest = a0 + 4;
+        if (hit >= 0) {
+          bu_mark_found(P, L, sm, w0, v[k], d, acc);
+          if (STATS) acc.edges += (unsigned long long)(hit - s[k] + 1);
+        } else if (rest < e[k]) {
+          const int slot = atomicAdd(&sm.npend, 1);
+          sm.pstart[slot] = rest;
+          sm.plen[slot] = (int)(e[k] - rest);
+          sm.pv[slot] = v[k];
+          sm.pd[slot] = d;
+          sm.pex[slot] = (int)(rest - s[k]);
+        } else if (STATS) {
+          acc.edges += (unsigned long long)d;
+        }
       }
     }
     __syncwarp();
-    if (sm.npend > 0) bu_drain<STATS>(P, L, front, sm, w0, acc);
+    if (sm.npend >= kDrainMin) bu_drain<STATS>(P, L, front, sm, w0, acc);
   }
   if (sm.npend > 0) bu_drain<STATS>(P, L, front, sm, w0, acc);
   __syncwarp();
@@ -735,11 +821,13 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
   __syncwarp();
 }
 
-// Bottom-up level.  Batches of 32 words go to warps statically (interleaved,
-// bu_chunk = 0) or bu_chunk batches at a time from a shared cursor, the next
-// grab being requested before the current one is processed.
+// Bottom-up level.  Batches of 32 words go to warps statically (interleaved:
+// bu_chunk = 0, or a level with fewer unvisited vertices than bitmap words,
+// where most batches are empty and a shared cursor would only add atomics) or
+// bu_chunk batches at a time from a shared cursor, the next grab being
+// requested before the current one is processed.
 template <typename RP, bool STATS>
-__device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigned* next) {
+__device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigned* next, bool dyn) {
   extern __shared__ unsigned long long g_dyn_smem[];  // blockDim.x / 32 BuWarpSmem records
   BuWarpSmem& sm = reinterpret_cast<BuWarpSmem*>(g_dyn_smem)[threadIdx.x >> 5];
   Slot* out = &P.ctrl->slot[(L + 1) & 3];
@@ -748,7 +836,7 @@ __device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigne
   if (lane == 0) sm.npend = 0;
   __syncwarp();
   Acc acc;
-  if (P.bu_chunk <= 0) {
+  if (P.bu_chunk <= 0 || !dyn) {
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long b = gw; b < nbatch; b += nwarps) bu_batch<RP, STATS>(P, L, front, next, b * 32, sm, acc);
@@ -805,8 +893,14 @@ __device__ void convert_phase(const KParams& P, int L, long long nf) {
     int d = 0;
     if (i < nf) {
       const int v = qv[i];
-      s = rp_at<RP>(P.rp, v);
-      d = (int)(rp_at<RP>(P.rp, (long long)v + 1) - s);
+      if (P.head) {
+        const int4 h = __ldg(P.head + v);
+        s = h.z;
+        d = h.w;
+      } else {
+        s = rp_at<RP>(P.rp, v);
+        d = (int)(rp_at<RP>(P.rp, (long long)v + 1) - s);
+      }
     }
     const int ni = (d + P.chunk - 1) / P.chunk;
     const bool hub = d >= P.small_max && ni > 32;
@@ -836,6 +930,12 @@ __device__ void convert_phase(const KParams& P, int L, long long nf) {
 }
 
 // ---------------------------------------------------------------- level loop
+
+// Dynamic batch assignment for a bottom-up level only while at least one
+// unvisited vertex of degree > 0 per bitmap word remains.
+__host__ __device__ inline bool bu_dynamic(const KParams& P, long long reached) {
+  return P.n_live - reached >= (long long)P.nw;
+}
 
 struct LoopState {
   int L = 0;
@@ -890,7 +990,7 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
       td_phase<RP, STATS>(P, L, items, mega);
     } else {
       ++bul;
-      bu_phase<RP, STATS>(P, L, st.fb ? P.bm1 : P.bm0, st.fb ? P.bm0 : P.bm1);
+      bu_phase<RP, STATS>(P, L, st.fb ? P.bm1 : P.bm0, st.fb ? P.bm0 : P.bm1, bu_dynamic(P, st.reached));
     }
     if (!grid_barrier(P, epoch)) return;
     Slot* nx = &P.ctrl->slot[(L + 1) & 3];
@@ -951,7 +1051,7 @@ __global__ void __launch_bounds__(1024) k_init_seed(KParams P) {
 
 template <typename RP, bool STATS>
 __global__ void __launch_bounds__(1024) k_level(KParams P, int L, int td, int fb, unsigned long long items,
-                                                unsigned long long mega) {
+                                                unsigned long long mega, long long reached) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Slot* z = &P.ctrl->slot[(L + 2) & 3];
     z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0; z->mega = 0;
@@ -959,7 +1059,7 @@ __global__ void __launch_bounds__(1024) k_level(KParams P, int L, int td, int fb
   if (td) {
     td_phase<RP, STATS>(P, L, items, mega);
   } else {
-    bu_phase<RP, STATS>(P, L, fb ? P.bm1 : P.bm0, fb ? P.bm0 : P.bm1);
+    bu_phase<RP, STATS>(P, L, fb ? P.bm1 : P.bm0, fb ? P.bm0 : P.bm1, bu_dynamic(P, reached));
   }
 }
 
@@ -1009,6 +1109,8 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
   K.nw = g->nw;
   K.src = src;
   K.init_vis = g->init_vis;
+  K.head = g->head;
+  K.n_live = g->n - g->isolated;
   K.dist = dist;
   K.vis = ws.vis;
   K.bm0 = ws.bm[0];
@@ -1075,7 +1177,7 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
   bool td = true;
   Ctrl host_tot{};
   for (;;) {
-    k_level<RP, STATS><<<grid, block, smem, stream>>>(K, L, td ? 1 : 0, fb, items, mega);
+    k_level<RP, STATS><<<grid, block, smem, stream>>>(K, L, td ? 1 : 0, fb, items, mega, reached);
     GBFS_CUDA(cudaGetLastError());
     if (td) ++tdl; else ++bul;
     GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,

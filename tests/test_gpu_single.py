@@ -48,8 +48,9 @@ def run(B, g, src, n, stream=None, **kw):
 
 
 def check(B, rp, col, srcs, rp_bits=64, policies=POLICIES, launches=(0, 1), extra=None, check_stats=True,
-          degree_order=False):
+          degree_order=False, head=True):
     flags = B.BFS_VALIDATE | B.BFS_VALIDATE_SYMMETRY | (B.BFS_DEGREE_ORDER if degree_order else 0)
+    flags |= 0 if head else B.BFS_NO_HEAD
     g = B.bfs_graph_upload(rp, col, flags=flags, row_ptr_bits=rp_bits)
     n = len(rp) - 1
     for src in srcs:
@@ -69,12 +70,13 @@ def check(B, rp, col, srcs, rp_bits=64, policies=POLICIES, launches=(0, 1), extr
     g.free()
 
 
-def test_closed_form_graphs(bfs):
+@pytest.mark.parametrize("head", [True, False])
+def test_closed_form_graphs(bfs, head):
     cases = [G.path_graph(1), G.path_graph(2), G.path_graph(100), G.star_graph(40), G.complete_graph(9),
              G.cycle_graph(33), graphgen.grid2d(7, 45)]
     for rp, col in cases:
         n = len(rp) - 1
-        check(bfs, rp, col, sorted({0, n // 2, n - 1}))
+        check(bfs, rp, col, sorted({0, n // 2, n - 1}), head=head)
 
 
 def test_disjoint_union_and_isolated(bfs):
@@ -90,10 +92,10 @@ def test_rmat_s16_td(bfs):
     check(bfs, rp, col, srcs, rp_bits=32, policies={"td_only": dict(policy=3)}, launches=(0, 1, 2))
 
 
-@pytest.mark.parametrize("bits", [32, 64])
-def test_rmat_s14_all_policies(bfs, bits):
+@pytest.mark.parametrize("bits,head", [(32, True), (64, True), (32, False), (64, False)])
+def test_rmat_s14_all_policies(bfs, bits, head):
     rp, col = graphgen.rmat(14, seed=7)
-    check(bfs, rp, col, graphgen.sources(rp, 3, 1002), rp_bits=bits)
+    check(bfs, rp, col, graphgen.sources(rp, 3, 1002), rp_bits=bits, head=head)
 
 
 def test_er_and_rgg_and_grid(bfs):
@@ -114,9 +116,10 @@ def test_er_and_rgg_and_grid(bfs):
     dict(bu_thread_max=4, bu_warp_min=0),
     dict(bu_thread_max=1 << 20, bu_warp_min=1 << 24),
 ])
-def test_parameter_extremes(bfs, params):
+@pytest.mark.parametrize("head", [True, False])
+def test_parameter_extremes(bfs, params, head):
     rp, col = graphgen.rmat(13, seed=9)
-    check(bfs, rp, col, graphgen.sources(rp, 2, 1004), extra=params,
+    check(bfs, rp, col, graphgen.sources(rp, 2, 1004), extra=params, head=head,
           policies={k: POLICIES[k] for k in ("edges", "bu_from_1", "script_rand")})
 
 
