@@ -107,10 +107,12 @@ typedef struct bfs_params {
     int32_t test_barrier_extra; /* testing only: grid barriers wait for this many blocks more than
                                    were launched, so a wait runs out and BFS_ETIMEOUT is returned */
     int32_t bu_chunk;        /* bottom-up: groups of 32 bitmap words a warp takes per grab from a shared
-                                cursor (0 = static interleaved assignment; default 1) */
-    int32_t bu_thread_max;   /* bottom-up: a vertex whose parent is not among its first aligned four
-                                entries keeps scanning on its own lane for up to this many more
-                                entries before the warp takes over (default 32) */
+                                cursor (0 = static interleaved assignment, default; levels with fewer
+                                unvisited vertices than bitmap words are always static) */
+    int32_t bu_thread_max;   /* bottom-up: a vertex whose parent is not among its first entries (the
+                                two of the head table, else the first aligned four) keeps scanning on
+                                its own lane for up to this many more entries before the warp takes
+                                over (default 32) */
     int32_t ms_lanes;        /* bfs_multi: sources per group (1..256, default 256) */
     int32_t ms_ring;         /* bfs_multi: frontier levels kept before they are written out (2..8,
                                 default 8) */
@@ -216,7 +218,10 @@ int bfs_single(bfs_graph *g, int32_t src, int32_t *dist, void *stream);
  *  params       NULL = defaults.
  *  stats        NULL, or receives the query's totals.
  *  levels       NULL, or an array of level_cap entries receiving per-level
- *               counters for levels 0..min(levels, level_cap)-1.
+ *               records for levels 0..min(levels, level_cap)-1: direction,
+ *               converted, frontier, found and (persistent launch) ns always;
+ *               edges and unvisited only when stats is non-NULL (the counting
+ *               variant of the kernel runs only then).  Unused entries stay zero.
  */
 int bfs_single_ex(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *params,
                   bfs_stats *stats, bfs_level_stat *levels, int32_t level_cap, void *stream);

@@ -307,15 +307,24 @@ def bfs_single(g: Graph, src: int, dist, stream=None):
 
 def bfs_single_ex(g: Graph, src: int, dist, params: bfs_params | None = None, stats: bool = False,
                   level_cap: int = 0, stream=None):
-    """bfs_single with parameters; returns (stats dict or None, list of level dicts)."""
-    st = bfs_stats() if (stats or level_cap > 0) else None
+    """bfs_single with parameters; returns (stats dict or None, list of level dicts).
+
+    Level records without ``stats`` come from the production (non-counting)
+    kernel: direction, converted, frontier, found and ns; edges and unvisited
+    are filled only with ``stats=True``."""
+    st = bfs_stats() if stats else None
     lv = (bfs_level_stat * level_cap)() if level_cap > 0 else None
     rc = load().bfs_single_ex(g.handle, int(src), _ptr(dist), ctypes.byref(params) if params is not None else None,
                               ctypes.byref(st) if st is not None else None,
                               ctypes.cast(lv, ctypes.c_void_p) if lv is not None else None, level_cap,
                               _stream_handle(stream))
     _check(rc, "bfs_single_ex")
-    levels = [lv[i].as_dict() for i in range(min(st.levels, level_cap))] if lv is not None else []
+    levels = []
+    if lv is not None:
+        # every level has a non-empty frontier; unused entries stay zero
+        nl = min(st.levels, level_cap) if st is not None else next(
+            (i for i in range(level_cap) if lv[i].frontier == 0), level_cap)
+        levels = [lv[i].as_dict() for i in range(nl)]
     return (st.as_dict() if st is not None else None), levels
 
 

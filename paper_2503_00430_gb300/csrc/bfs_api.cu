@@ -202,6 +202,7 @@ int ensure_single_ws(bfs_graph* g) {
   const size_t nwb = sizeof(unsigned) * (size_t)g->nw;
   ws.cap = g->n + g->m / 256 + 2;
   GBFS_CUDA(cudaMalloc(&ws.vis, nwb));
+  GBFS_CUDA(cudaMalloc(&ws.lv8, (size_t)(g->n + 15) / 16 * 16));
   for (int i = 0; i < 2; ++i) {
     GBFS_CUDA(cudaMalloc(&ws.bm[i], nwb));
     GBFS_CUDA(cudaMemset(ws.bm[i], 0, nwb));
@@ -232,6 +233,7 @@ void free_single_ws(bfs_graph* g) {
   }
   cudaFree(ws.ctrl);
   cudaFree(ws.dist_tmp);
+  cudaFree(ws.lv8);
   cudaFree(ws.lst);
   if (ws.h_ctrl) cudaFreeHost(ws.h_ctrl);
   if (ws.h_slot) cudaFreeHost(ws.h_slot);
@@ -294,7 +296,7 @@ void bfs_params_default(bfs_params* p) {
   p->timeout_ms = 10000;
   p->script = 0;
   p->test_barrier_extra = 0;
-  p->bu_chunk = 1;
+  p->bu_chunk = 0;
   p->bu_thread_max = 32;
   p->ms_lanes = 256;
   p->ms_ring = 8;

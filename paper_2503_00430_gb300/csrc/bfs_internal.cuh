@@ -17,7 +17,7 @@ struct Slot {
   unsigned long long items;  // low 32 bits: small work items, high 32 bits: large work items
   unsigned long long nv;     // |F_L|
   unsigned long long mf;     // sum of degrees over F_L
-  unsigned long long nq;     // vertex-queue entries written by a bitmap -> queue conversion
+  unsigned long long nq;     // reserved (zeroed with the slot)
   unsigned long long cursor; // bottom-up: next bitmap word to hand out (dynamic assignment)
   unsigned long long mega;   // hub records: low 26 bits record count, high 38 bits chunk count
 };
@@ -54,6 +54,8 @@ struct KParams {
                              // (-1 for a missing neighbour), or null: read rp / col instead
   long long n_live;          // vertices of degree > 0 (n when unknown)
   int* dist;
+  unsigned char* lv8;        // per-vertex level bytes (255 = not reached) while the search runs, or
+                             // null: levels go straight to dist
   unsigned* vis;
   unsigned* bm0;
   unsigned* bm1;
@@ -109,6 +111,7 @@ __host__ __device__ inline bool next_is_top_down(int policy, int alpha, int beta
 struct SingleWs {
   bool ready = false;
   unsigned* vis = nullptr;
+  unsigned char* lv8 = nullptr;  // n bytes (rounded up to 16)
   unsigned* bm[2] = {nullptr, nullptr};
   int* qv[2] = {nullptr, nullptr};
   unsigned long long* it[2] = {nullptr, nullptr};

@@ -131,6 +131,7 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   K.src = src;
   K.init_vis = reinterpret_cast<unsigned*>(b + lay.init_vis);
   K.head = nullptr;
+  K.lv8 = nullptr;
   K.n_live = n;
   K.dist = dist;
   K.vis = reinterpret_cast<unsigned*>(b + lay.vis);

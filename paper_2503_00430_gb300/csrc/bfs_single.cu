@@ -66,13 +66,52 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Asynchronous 16-byte global -> shared copy (zero-filled when src_bytes is 0).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// L2 eviction-priority policies: data read once per level (adjacency, head
+// records) is marked evict-first, the small per-vertex state that every level
+// updates (level bytes) evict-last, so the streaming reads do not push it out.
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void st_u8_last(unsigned char* p, unsigned v) {
+  asm volatile("st.global.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(policy_evict_last()) : "memory");
+}
+__device__ __forceinline__ void st_v4_last(void* p, unsigned a, unsigned b, unsigned c, unsigned d) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(a), "r"(b), "r"(c),
+               "r"(d), "l"(policy_evict_last())
+               : "memory");
+}
+// Asynchronous 16-byte global -> shared copy, evict-first in L2 (zero-filled
+// when src_bytes is 0).
+__device__ __forceinline__ void cp_async16_first(void* smem, const void* gmem, int src_bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(sa), "l"(gmem),
+               "r"(src_bytes), "l"(policy_evict_first())
+               : "memory");
+}
+__device__ __forceinline__ int4 ldg4_first(const int* p) {
+  int4 q;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w)
+               : "l"(p), "l"(policy_evict_first()));
+  return q;
+}
+
+// The level of vertex v is L + 1: a level byte while the search keeps them
+// (direct = false), else its int32 distance.
+__device__ __forceinline__ void mark_level(const KParams& P, bool direct, int v, int L) {
+  if (direct) P.dist[v] = L + 1;
+  else st_u8_last(P.lv8 + v, (unsigned)(L + 1));
+}
 
 template <typename RP>
 __device__ __forceinline__ long long rp_at(const void* rp, long long i) {
@@ -188,11 +227,19 @@ __device__ void flush_acc(const KParams& P, int L, Acc& a, Slot* out, bool botto
 
 // dist[:] = -1 except dist[src] = 0; visited = degree-0/padding mask | src bit.
 template <typename RP>
-__device__ void init_phase(const KParams& P) {
+__device__ __noinline__ void init_phase(const KParams& P) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long n = P.n;
-  if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
+  if (P.lv8) {
+    // Level bytes: 255 everywhere (the allocation is rounded up to 16 bytes), 0 at src.
+    const long long n16 = (n + 15) >> 4;
+    for (long long i = tid; i < n16; i += nth) {
+      unsigned w[4] = {kFull, kFull, kFull, kFull};
+      if ((long long)(P.src >> 4) == i) w[(P.src >> 2) & 3] &= ~(0xffu << (8 * (P.src & 3)));
+      st_v4_last(P.lv8 + 16 * i, w[0], w[1], w[2], w[3]);
+    }
+  } else if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
     int4* d4 = reinterpret_cast<int4*>(P.dist);
     const long long n4 = n >> 2;
     for (long long i = tid; i < n4; i += nth) {
@@ -218,9 +265,37 @@ __device__ void init_phase(const KParams& P) {
   }
 }
 
+// dist[v] = level byte of v, or -1 where it is 255 (every vertex written).
+__device__ __noinline__ void expand_phase(const KParams& P) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long n = P.n;
+  long long done = 0;
+  if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
+    const long long n4 = n >> 2;
+    const unsigned* l4 = reinterpret_cast<const unsigned*>(P.lv8);
+    int4* d4 = reinterpret_cast<int4*>(P.dist);
+    for (long long i = tid; i < n4; i += nth) {
+      const unsigned b = l4[i];
+      int x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int t = (int)((b >> (8 * k)) & 0xffu);
+        x[k] = t == 255 ? -1 : t;
+      }
+      __stcs(d4 + i, make_int4(x[0], x[1], x[2], x[3]));
+    }
+    done = n4 << 2;
+  }
+  for (long long i = done + tid; i < n; i += nth) {
+    const int t = P.lv8[i];
+    P.dist[i] = t == 255 ? -1 : t;
+  }
+}
+
 // Level-0 frontier {src}: vertex queue, work items and counters of slot 0.
 template <typename RP>
-__device__ void seed_phase(const KParams& P) {
+__device__ __noinline__ void seed_phase(const KParams& P) {
   const long long s = rp_at<RP>(P.rp, P.src);
   const long long d = rp_at<RP>(P.rp, (long long)P.src + 1) - s;
   Slot* sl = &P.ctrl->slot[0];
@@ -290,7 +365,7 @@ __device__ __forceinline__ void append_hubs(const KParams& P, unsigned mask, con
 // frontier: vertex queue and degree-binned work items, one set of atomics per
 // warp.
 template <typename RP>
-__device__ __forceinline__ void td_visit4(const KParams& P, int L, const int (&c)[4], Slot* out, int* qvn,
+__device__ __forceinline__ void td_visit4(const KParams& P, int L, bool direct, const int (&c)[4], Slot* out, int* qvn,
                                           unsigned long long* itn, MegaRec* mgn) {
   unsigned cur[4];
 #pragma unroll
@@ -313,7 +388,7 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, const int (&c
     s[k] = 0;
     d[k] = 0;
     if ((cl >> k) & 1u) {
-      P.dist[c[k]] = L + 1;
+      mark_level(P, direct, c[k], L);
       if (P.head) {
         const int4 h = __ldg(P.head + c[k]);
         s[k] = h.z;
@@ -397,8 +472,28 @@ __device__ __forceinline__ int owner_of(int excl, int e) {
   return lo;
 }
 
+// Warp-collective: visit the entries [s, e) of one adjacency span, 128 per
+// step through aligned 128-bit loads (four candidates per lane).
+template <typename RP>
+__device__ __forceinline__ void td_span(const KParams& P, int L, bool direct, long long s, long long e, Slot* out, int* qvn,
+                                        unsigned long long* itn, MegaRec* mgn) {
+  const unsigned lane = lane_id();
+  for (long long base = s & ~3ll; base < e; base += 128) {
+    const long long j = base + 4 * (long long)lane;
+    int4 q = make_int4(-1, -1, -1, -1);
+    if (j < e) q = ldg4_first(P.col + j);
+    const int c[4] = {(j >= s && j < e) ? q.x : -1, (j + 1 >= s && j + 1 < e) ? q.y : -1,
+                      (j + 2 >= s && j + 2 < e) ? q.z : -1, (j + 3 >= s && j + 3 < e) ? q.w : -1};
+    td_visit4<RP>(P, L, direct, c, out, qvn, itn, mgn);
+  }
+}
+
+// Top-down level.  The level's work is one index space: groups of 32 small
+// items, then large items (<= chunk entries each), then hub chunk tickets;
+// warps take indices in block-major order (consecutive indices go to
+// different blocks), so no warp holds work of two kinds while others idle.
 template <typename RP, bool STATS>
-__device__ void td_phase(const KParams& P, int L, unsigned long long items_cur, unsigned long long mega_cur) {
+__device__ void td_phase(const KParams& P, int L, bool direct, unsigned long long items_cur, unsigned long long mega_cur) {
   const unsigned long long nsmall = items_cur & 0xffffffffull, nlarge = items_cur >> 32;
   const unsigned long long* it = (L & 1) ? P.it1 : P.it0;
   unsigned long long* itn = (L & 1) ? P.it0 : P.it1;
@@ -407,77 +502,63 @@ __device__ void td_phase(const KParams& P, int L, unsigned long long items_cur, 
   int* qvn = (L & 1) ? P.qv0 : P.qv1;
   Slot* out = &P.ctrl->slot[(L + 1) & 3];
   const unsigned lane = lane_id();
-  // Block-major warp order: consecutive work goes to different blocks (SMs).
   const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  Acc acc;
-  // Small items: 32 per warp; their edges are dealt to the lanes through an
-  // exclusive scan of the lengths, 128 per step (four per lane).
-  for (long long g = gw; (unsigned long long)g * 32ull < nsmall; g += nwarps) {
-    const unsigned long long i = (unsigned long long)g * 32ull + lane;
-    const unsigned long long item = i < nsmall ? it[i] : 0ull;
-    const long long s = (long long)(item >> 16);
-    const int len = (int)(item & 0xffffull);
-    const int incl = warp_incl_scan(len);
-    const int excl = incl - len;
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (STATS) acc.edges += (unsigned long long)len;
-    for (int base = 0; base < total; base += 128) {
-      int c[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int e = base + 32 * k + (int)lane;
-        const int o = owner_of(excl, e);
-        const long long so = __shfl_sync(kFull, s, o);
-        const int exo = __shfl_sync(kFull, excl, o);
-        c[k] = e < total ? __ldg(P.col + so + (e - exo)) : -1;
-      }
-      td_visit4<RP>(P, L, c, out, qvn, itn, mgn);
-    }
-  }
-  // Large items (<= chunk edges each): one warp per item, 128-bit loads of the aligned span.
-  for (long long i = gw; (unsigned long long)i < nlarge; i += nwarps) {
-    const unsigned long long item = it[P.cap - 1 - i];
-    const long long s = (long long)(item >> 16);
-    const int len = (int)(item & 0xffffull);
-    const long long e = s + len;
-    if (STATS && lane == 0) acc.edges += (unsigned long long)len;
-    for (long long base = s & ~3ll; base < e; base += 128) {
-      const long long j = base + 4 * (long long)lane;
-      int4 q = make_int4(-1, -1, -1, -1);
-      if (j < e) q = __ldg(reinterpret_cast<const int4*>(P.col + j));
-      const int c[4] = {(j >= s && j < e) ? q.x : -1, (j + 1 >= s && j + 1 < e) ? q.y : -1,
-                        (j + 2 >= s && j + 2 < e) ? q.z : -1, (j + 3 >= s && j + 3 < e) ? q.w : -1};
-      td_visit4<RP>(P, L, c, out, qvn, itn, mgn);
-    }
-  }
-  // Hub chunks: ticket t belongs to the last record whose base is <= t (a
-  // 32-way search over the records, which are ordered by base).
+  const long long ngroups = (long long)((nsmall + 31ull) / 32ull);
   const long long nrec = (long long)(mega_cur & ((1ull << kMegaCountBits) - 1));
   const long long nch = (long long)(mega_cur >> kMegaCountBits);
-  for (long long t = gw; t < nch; t += nwarps) {
-    long long lo = 0, hi = nrec;
-    while (hi - lo > 1) {
-      const long long step = (hi - lo + 31) / 32;
-      const long long idx = lo + (long long)lane * step;
-      const bool ok = idx < hi && (long long)mg[idx].base <= t;
-      const unsigned bm = __ballot_sync(kFull, ok);
-      const long long k = 31 - __clz(bm);
-      lo = lo + k * step;
-      hi = lo + step < hi ? lo + step : hi;
-    }
-    const long long o = (t - (long long)mg[lo].base) * P.chunk;
-    const long long hd = mg[lo].deg;
-    const long long s = mg[lo].start + o;
-    const long long e = s + (hd - o < P.chunk ? hd - o : P.chunk);
-    if (STATS && lane == 0) acc.edges += (unsigned long long)(e - s);
-    for (long long base = s & ~3ll; base < e; base += 128) {
-      const long long j = base + 4 * (long long)lane;
-      int4 q = make_int4(-1, -1, -1, -1);
-      if (j < e) q = __ldg(reinterpret_cast<const int4*>(P.col + j));
-      const int c[4] = {(j >= s && j < e) ? q.x : -1, (j + 1 >= s && j + 1 < e) ? q.y : -1,
-                        (j + 2 >= s && j + 2 < e) ? q.z : -1, (j + 3 >= s && j + 3 < e) ? q.w : -1};
-      td_visit4<RP>(P, L, c, out, qvn, itn, mgn);
+  const long long nwork = ngroups + (long long)nlarge + nch;
+  Acc acc;
+  for (long long u = gw; u < nwork; u += nwarps) {
+    if (u < ngroups) {
+      // 32 small items; their entries are dealt to the lanes through an
+      // exclusive scan of the lengths, 128 per step (four per lane).
+      const unsigned long long i = (unsigned long long)u * 32ull + lane;
+      const unsigned long long item = i < nsmall ? it[i] : 0ull;
+      const long long s = (long long)(item >> 16);
+      const int len = (int)(item & 0xffffull);
+      const int incl = warp_incl_scan(len);
+      const int excl = incl - len;
+      const int total = __shfl_sync(kFull, incl, 31);
+      if (STATS) acc.edges += (unsigned long long)len;
+      for (int base = 0; base < total; base += 128) {
+        int c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = base + 32 * k + (int)lane;
+          const int o = owner_of(excl, e);
+          const long long so = __shfl_sync(kFull, s, o);
+          const int exo = __shfl_sync(kFull, excl, o);
+          c[k] = e < total ? __ldg(P.col + so + (e - exo)) : -1;
+        }
+        td_visit4<RP>(P, L, direct, c, out, qvn, itn, mgn);
+      }
+    } else if (u < ngroups + (long long)nlarge) {
+      const unsigned long long item = it[P.cap - 1 - (u - ngroups)];
+      const long long s = (long long)(item >> 16);
+      const int len = (int)(item & 0xffffull);
+      if (STATS && lane == 0) acc.edges += (unsigned long long)len;
+      td_span<RP>(P, L, direct, s, s + len, out, qvn, itn, mgn);
+    } else {
+      // Hub chunk ticket t belongs to the last record whose base is <= t (a
+      // 32-way search over the records, which are ordered by base).
+      const long long t = u - ngroups - (long long)nlarge;
+      long long lo = 0, hi = nrec;
+      while (hi - lo > 1) {
+        const long long step = (hi - lo + 31) / 32;
+        const long long idx = lo + (long long)lane * step;
+        const bool ok = idx < hi && (long long)mg[idx].base <= t;
+        const unsigned bm = __ballot_sync(kFull, ok);
+        const long long k = 31 - __clz(bm);
+        lo = lo + k * step;
+        hi = lo + step < hi ? lo + step : hi;
+      }
+      const long long o = (t - (long long)mg[lo].base) * P.chunk;
+      const long long hd = mg[lo].deg;
+      const long long s = mg[lo].start + o;
+      const long long e = s + (hd - o < P.chunk ? hd - o : P.chunk);
+      if (STATS && lane == 0) acc.edges += (unsigned long long)(e - s);
+      td_span<RP>(P, L, direct, s, e, out, qvn, itn, mgn);
     }
   }
   if (STATS) flush_acc<STATS>(P, L, acc, out, false);
@@ -510,10 +591,10 @@ struct BuWarpSmem {
   int npend;
 };
 
-__device__ __forceinline__ void bu_mark_found(const KParams& P, int L, BuWarpSmem& sm, long long w0, int v, int d,
+__device__ __forceinline__ void bu_mark_found(const KParams& P, int L, bool direct, BuWarpSmem& sm, long long w0, int v, int d,
                                               Acc& acc) {
   atomicOr(&sm.next[(int)((long long)v / 32 - w0)], 1u << (v & 31));
-  P.dist[v] = L + 1;
+  mark_level(P, direct, v, L);
   acc.found += 1;
   acc.mf += (unsigned long long)d;
 }
@@ -524,7 +605,7 @@ __device__ __forceinline__ void bu_mark_found(const KParams& P, int L, BuWarpSme
 // vertex's remaining entries are skipped once it has found a parent.  Ranges
 // longer than bu_warp_min are scanned one at a time by the whole warp.
 template <bool STATS>
-__device__ void bu_drain(const KParams& P, int L, const unsigned* front, BuWarpSmem& sm, long long w0, Acc& acc) {
+__device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* front, BuWarpSmem& sm, long long w0, Acc& acc) {
   const unsigned lane = lane_id();
   __syncwarp();
   const int np = sm.npend;
@@ -638,7 +719,7 @@ __device__ void bu_drain(const KParams& P, int L, const unsigned* front, BuWarpS
         ex += (int)hx;
       }
     }
-    if (found) bu_mark_found(P, L, sm, w0, pv, pdeg, acc);
+    if (found) bu_mark_found(P, L, direct, sm, w0, pv, pdeg, acc);
     if (STATS && have) acc.edges += (unsigned long long)ex;
   }
   __syncwarp();
@@ -671,11 +752,10 @@ __device__ __forceinline__ void round_vertices(unsigned act, int excl, int total
 // entries, is queued for bu_drain.  New-frontier bits are gathered in shared
 // memory and stored once per word, together with the updated visited word.
 template <typename RP, bool STATS>
-__device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigned* next, long long w0,
-                         BuWarpSmem& sm, Acc& acc) {
+__device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* front, unsigned* next, long long w0,
+                         unsigned vw, BuWarpSmem& sm, Acc& acc) {
   const unsigned lane = lane_id();
   const long long w = w0 + lane;
-  const unsigned vw = w < P.nw ? P.vis[w] : kFull;
   const unsigned act = ~vw;  // padding bits past n are set in vis, so act holds vertices < n only
   sm.next[lane] = 0u;
   const int cnt = __popc(act);
@@ -690,7 +770,7 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
     round_vertices(act, excl, total, w0, 0, vn);
 #pragma unroll
     for (int k = 0; k < kBuU; ++k)
-      cp_async16(&sm.hbuf[0][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
+      cp_async16_first(&sm.hbuf[0][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
     cp_async_commit();
   }
   for (int r0 = 0, buf = 0; r0 < total; r0 += 32 * kBuU, buf ^= 1) {
@@ -707,7 +787,7 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
         round_vertices(act, excl, total, w0, r0 + 32 * kBuU, vn);
 #pragma unroll
         for (int k = 0; k < kBuU; ++k)
-          cp_async16(&sm.hbuf[buf ^ 1][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
+          cp_async16_first(&sm.hbuf[buf ^ 1][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
       }
       cp_async_commit();
       cp_async_wait1();
@@ -725,7 +805,7 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
         if (v[k] < 0) continue;
         const int d = hd[k].w;
         if (f0[k] | f1[k]) {
-          bu_mark_found(P, L, sm, w0, v[k], d, acc);
+          bu_mark_found(P, L, direct, sm, w0, v[k], d, acc);
           if (STATS) acc.edges += f0[k] ? 1ull : 2ull;
         } else if (d > 2) {
           const int slot = atomicAdd(&sm.npend, 1);
@@ -778,7 +858,7 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
         const int d = (int)(e[k] - s[k]);
         const long long rest = a0 + 4;
         if (hit >= 0) {
-          bu_mark_found(P, L, sm, w0, v[k], d, acc);
+          bu_mark_found(P, L, direct, sm, w0, v[k], d, acc);
           if (STATS) acc.edges += (unsigned long long)(hit - s[k] + 1);
         } else if (rest < e[k]) {
           const int slot = atomicAdd(&sm.npend, 1);
@@ -793,41 +873,32 @@ __device__ void bu_batch(const KParams& P, int L, const unsigned* front, unsigne
       }
     }
     __syncwarp();
-    if (sm.npend >= kDrainMin) bu_drain<STATS>(P, L, front, sm, w0, acc);
+    if (sm.npend >= kDrainMin) bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
   }
-  if (sm.npend > 0) bu_drain<STATS>(P, L, front, sm, w0, acc);
+  if (sm.npend > 0) bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
   __syncwarp();
   const unsigned nx = sm.next[lane];
   if (w < P.nw) {
     next[w] = nx;
     if (nx) P.vis[w] = vw | nx;  // this warp is the only writer of its batch's words
   }
-  // Vertex queue of the new frontier (read by a later change of direction).
-  const int fc = __popc(nx);
-  const int f_incl = warp_incl_scan(fc);
-  const int f_tot = __shfl_sync(kFull, f_incl, 31);
-  if (f_tot) {
-    unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(&P.ctrl->slot[(L + 1) & 3].nq, (unsigned long long)f_tot);
-    base = __shfl_sync(kFull, base, 31) + (unsigned long long)(f_incl - fc);
-    int* qvn = ((L + 1) & 1) ? P.qv1 : P.qv0;
-    unsigned t = nx;
-    while (t) {
-      const int b = __ffs(t) - 1;
-      t &= t - 1;
-      qvn[base++] = (int)(w * 32 + b);
-    }
-  }
   __syncwarp();
+}
+
+// Visited word of lane `lane` in the batch starting at word w0 (all-set past the end).
+__device__ __forceinline__ unsigned batch_word(const KParams& P, long long w0) {
+  const long long w = w0 + lane_id();
+  return w < P.nw ? P.vis[w] : kFull;
 }
 
 // Bottom-up level.  Batches of 32 words go to warps statically (interleaved:
 // bu_chunk = 0, or a level with fewer unvisited vertices than bitmap words,
 // where most batches are empty and a shared cursor would only add atomics) or
-// bu_chunk batches at a time from a shared cursor, the next grab being
-// requested before the current one is processed.
+// bu_chunk batches at a time from a shared cursor.  A warp requests its next
+// grab (and loads the visited words of its next batch) before it processes
+// the current batch, so neither latency sits between two batches.
 template <typename RP, bool STATS>
-__device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigned* next, bool dyn) {
+__device__ void bu_phase(const KParams& P, int L, bool direct, const unsigned* front, unsigned* next, bool dyn) {
   extern __shared__ unsigned long long g_dyn_smem[];  // blockDim.x / 32 BuWarpSmem records
   BuWarpSmem& sm = reinterpret_cast<BuWarpSmem*>(g_dyn_smem)[threadIdx.x >> 5];
   Slot* out = &P.ctrl->slot[(L + 1) & 3];
@@ -839,19 +910,40 @@ __device__ void bu_phase(const KParams& P, int L, const unsigned* front, unsigne
   if (P.bu_chunk <= 0 || !dyn) {
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long b = gw; b < nbatch; b += nwarps) bu_batch<RP, STATS>(P, L, front, next, b * 32, sm, acc);
+    long long b = gw;
+    unsigned vw = b < nbatch ? batch_word(P, b * 32) : kFull;
+    while (b < nbatch) {
+      const long long bn = b + nwarps;
+      const unsigned vwn = bn < nbatch ? batch_word(P, bn * 32) : kFull;
+      bu_batch<RP, STATS>(P, L, direct, front, next, b * 32, vw, sm, acc);
+      b = bn;
+      vw = vwn;
+    }
   } else {
     unsigned long long* cur = &P.ctrl->slot[L & 3].cursor;
     const long long ch = P.bu_chunk;
-    long long b0 = 0;
-    if (lane == 0) b0 = (long long)atomicAdd(cur, (unsigned long long)ch);
-    b0 = __shfl_sync(kFull, b0, 0);
-    while (b0 < nbatch) {
-      long long b1 = 0;
-      if (lane == 0) b1 = (long long)atomicAdd(cur, (unsigned long long)ch);
-      const long long bend = b0 + ch < nbatch ? b0 + ch : nbatch;
-      for (long long b = b0; b < bend; ++b) bu_batch<RP, STATS>(P, L, front, next, b * 32, sm, acc);
-      b0 = __shfl_sync(kFull, b1, 0);
+    // Grabs of ch consecutive batches; `g1` is requested one grab ahead.
+    long long g0 = 0, g1 = 0;
+    if (lane == 0) {
+      g0 = (long long)atomicAdd(cur, (unsigned long long)ch);
+      g1 = (long long)atomicAdd(cur, (unsigned long long)ch);
+    }
+    g0 = __shfl_sync(kFull, g0, 0);
+    g1 = __shfl_sync(kFull, g1, 0);
+    unsigned vw = g0 < nbatch ? batch_word(P, g0 * 32) : kFull;
+    while (g0 < nbatch) {
+      long long g2 = 0;
+      if (lane == 0) g2 = (long long)atomicAdd(cur, (unsigned long long)ch);
+      const long long gend = g0 + ch < nbatch ? g0 + ch : nbatch;
+      for (long long b = g0; b < gend; ++b) {
+        // Next batch: the following one of this grab, else the first of the next grab.
+        const long long bn = b + 1 < gend ? b + 1 : g1;
+        const unsigned vwn = bn < nbatch ? batch_word(P, bn * 32) : kFull;
+        bu_batch<RP, STATS>(P, L, direct, front, next, b * 32, vw, sm, acc);
+        vw = vwn;
+      }
+      g0 = g1;
+      g1 = __shfl_sync(kFull, g2, 0);
     }
   }
   flush_acc<STATS>(P, L, acc, out, true);
@@ -875,55 +967,89 @@ __device__ void scatter_phase(const int* qv, long long nv, unsigned* bm) {
   }
 }
 
-// Bottom-up -> top-down: the work items of F_{L+1} from its vertex queue
-// (written by the bottom-up level), one vertex per lane.
+// Bottom-up -> top-down: the work items of F_{L+1} from its bitmap `fbm` (the
+// new-frontier bitmap of the last bottom-up level).  A warp scans 256 words per
+// step (eight per lane) and packs their set bits onto the lanes, one vertex per
+// lane per round, so a sparse frontier costs one round (and one atomic) per
+// 8192 vertices scanned.
 template <typename RP>
-__device__ void convert_phase(const KParams& P, int L, long long nf) {
+__device__ __noinline__ void convert_phase(const KParams& P, int L, const unsigned* fbm) {
   const int Ln = L + 1;
   unsigned long long* itn = (Ln & 1) ? P.it1 : P.it0;
-  const int* qv = (Ln & 1) ? P.qv1 : P.qv0;
   Slot* out = &P.ctrl->slot[Ln & 3];
   const unsigned lane = lane_id();
   const unsigned lt = lanemask_lt();
   const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long b0 = gw * 32; b0 < nf; b0 += nwarps * 32) {
-    const long long i = b0 + lane;
-    long long s = 0;
-    int d = 0;
-    if (i < nf) {
-      const int v = qv[i];
-      if (P.head) {
-        const int4 h = __ldg(P.head + v);
-        s = h.z;
-        d = h.w;
-      } else {
-        s = rp_at<RP>(P.rp, v);
-        d = (int)(rp_at<RP>(P.rp, (long long)v + 1) - s);
+  constexpr int kW = 8;  // bitmap words per lane: 8192 vertices per warp step (frontiers here are sparse)
+  const long long nstep = ((long long)P.nw + 32 * kW - 1) / (32 * kW);
+  for (long long bt = gw; bt < nstep; bt += nwarps) {
+    const long long w0 = bt * 32 * kW + (long long)lane * kW;
+    unsigned x[kW];
+    int cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kW; ++j) {
+      x[j] = w0 + j < P.nw ? fbm[w0 + j] : 0u;
+      cnt += __popc(x[j]);
+    }
+    const int incl = warp_incl_scan(cnt);
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(kFull, incl, 31);
+    for (int r0 = 0; r0 < total; r0 += 32) {
+      const int kk = r0 + (int)lane;
+      const int wo = owner_of(excl, kk);
+      int r = kk - __shfl_sync(kFull, excl, wo);
+      long long vw = -1;  // word of this lane's vertex
+      unsigned aw = 0;
+#pragma unroll
+      for (int j = 0; j < kW; ++j) {
+        const unsigned xj = __shfl_sync(kFull, x[j], wo);
+        const int c = __popc(xj);
+        if (kk < total && vw < 0) {
+          if (r < c) {
+            vw = bt * 32 * kW + (long long)wo * kW + j;
+            aw = xj;
+          } else {
+            r -= c;
+          }
+        }
       }
-    }
-    const int ni = (d + P.chunk - 1) / P.chunk;
-    const bool hub = d >= P.small_max && ni > 32;
-    const int nsm = (d > 0 && d < P.small_max) ? 1 : 0;
-    const int nlg = (d >= P.small_max && !hub) ? ni : 0;
-    {
-      const long long hs[4] = {s, 0, 0, 0};
-      const int hd[4] = {d, 0, 0, 0};
-      append_hubs(P, hub ? 1u : 0u, hs, hd, out, (Ln & 1) ? P.mg1 : P.mg0);
-    }
-    const unsigned smask = __ballot_sync(kFull, nsm);
-    const int lg_incl = warp_incl_scan(nlg);
-    const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
-    unsigned long long b_items = 0;
-    if (lane == 0)
-      b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
-    b_items = __shfl_sync(kFull, b_items, 0);
-    if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
-    if (nlg) {
-      unsigned long long bb = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
-      for (int o = 0; o < d; o += P.chunk) {
-        const int len = d - o < P.chunk ? d - o : P.chunk;
-        itn[P.cap - 1 - (long long)(bb++)] = pack_item(s + o, len);
+      long long s = 0;
+      int d = 0;
+      if (vw >= 0) {
+        const int v = (int)(vw * 32 + (long long)nth_set_bit(aw, r));
+        if (P.head) {
+          const int4 h = __ldg(P.head + v);
+          s = h.z;
+          d = h.w;
+        } else {
+          s = rp_at<RP>(P.rp, v);
+          d = (int)(rp_at<RP>(P.rp, (long long)v + 1) - s);
+        }
+      }
+      const int ni = (d + P.chunk - 1) / P.chunk;
+      const bool hub = d >= P.small_max && ni > 32;
+      const int nsm = (d > 0 && d < P.small_max) ? 1 : 0;
+      const int nlg = (d >= P.small_max && !hub) ? ni : 0;
+      {
+        const long long hs[4] = {s, 0, 0, 0};
+        const int hd[4] = {d, 0, 0, 0};
+        append_hubs(P, hub ? 1u : 0u, hs, hd, out, (Ln & 1) ? P.mg1 : P.mg0);
+      }
+      const unsigned smask = __ballot_sync(kFull, nsm);
+      const int lg_incl = warp_incl_scan(nlg);
+      const int lg_tot = __shfl_sync(kFull, lg_incl, 31);
+      unsigned long long b_items = 0;
+      if (lane == 0)
+        b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
+      b_items = __shfl_sync(kFull, b_items, 0);
+      if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
+      if (nlg) {
+        unsigned long long bb = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
+        for (int o = 0; o < d; o += P.chunk) {
+          const int len = d - o < P.chunk ? d - o : P.chunk;
+          itn[P.cap - 1 - (long long)(bb++)] = pack_item(s + o, len);
+        }
       }
     }
   }
@@ -949,7 +1075,7 @@ struct LoopState {
 template <bool STATS>
 __device__ void record_level(const KParams& P, const LoopState& st, long long found, int converted,
                              unsigned long long& t_mark) {
-  if (STATS && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (STATS || P.lst)) {
     const unsigned long long t = globaltimer_ns();
     if (P.lst && st.L < P.lst_cap) {
       P.lst[st.L].direction = st.td ? 0 : 1;
@@ -959,9 +1085,9 @@ __device__ void record_level(const KParams& P, const LoopState& st, long long fo
       P.lst[st.L].ns = (long long)(t - t_mark);
     }
     t_mark = t;
-    if (st.td) {
+    if (STATS && st.td) {
       P.ctrl->td_frontier += (unsigned long long)st.nf_cur;
-    } else {
+    } else if (STATS) {
       P.ctrl->bu_found += (unsigned long long)found;
     }
   }
@@ -969,75 +1095,126 @@ __device__ void record_level(const KParams& P, const LoopState& st, long long fo
 
 template <typename RP, bool STATS>
 __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
+  // Loop state lives in shared memory: thread 0 of every block reads the level
+  // counters after the barrier and decides (all blocks decide identically),
+  // so the phases run with no loop state held in registers.
+  struct LoopShared {
+    LoopState st;
+    unsigned long long items, mega, t_mark;
+    long long nf;
+    int action;  // 0 next level, 1 top-down -> bottom-up conversion, 2 bottom-up -> top-down, 3 done
+    int converted, conversions, tdl, bul;
+    int direct;  // levels are written to dist directly (no level bytes, or past level 254)
+  };
+  __shared__ LoopShared S;
   unsigned epoch = 0;
   init_phase<RP>(P);
   if (blockIdx.x == 0 && threadIdx.x == 0) seed_phase<RP>(P);
   if (!grid_barrier(P, epoch)) return;
-  LoopState st;
-  unsigned long long t_mark = STATS ? globaltimer_ns() : 0ull;
-  st.edges_visited = (long long)ld_relaxed_u64(&P.ctrl->slot[0].mf);
-  unsigned long long items = ld_relaxed_u64(&P.ctrl->slot[0].items);
-  unsigned long long mega = ld_relaxed_u64(&P.ctrl->slot[0].mega);
-  int converted = 0, conversions = 0, tdl = 0, bul = 0;
+  if (threadIdx.x == 0) {
+    S.st = LoopState();
+    S.st.edges_visited = (long long)ld_relaxed_u64(&P.ctrl->slot[0].mf);
+    S.items = ld_relaxed_u64(&P.ctrl->slot[0].items);
+    S.mega = ld_relaxed_u64(&P.ctrl->slot[0].mega);
+    S.t_mark = globaltimer_ns();
+    S.converted = S.conversions = S.tdl = S.bul = 0;
+    S.direct = P.lv8 == nullptr;
+  }
+  __syncthreads();
   for (;;) {
-    const int L = st.L;
+    const int L = S.st.L;
+    if (!S.direct && L >= 254) {
+      // Level bytes hold levels up to 254: from here on dist is written directly.
+      expand_phase(P);
+      if (!grid_barrier(P, epoch)) return;
+      if (threadIdx.x == 0) S.direct = 1;
+      __syncthreads();
+    }
+    const bool direct = S.direct != 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       Slot* z = &P.ctrl->slot[(L + 2) & 3];
       z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0; z->mega = 0;
     }
-    if (st.td) {
-      ++tdl;
-      td_phase<RP, STATS>(P, L, items, mega);
+    if (S.st.td) {
+      td_phase<RP, STATS>(P, L, direct, S.items, S.mega);
     } else {
-      ++bul;
-      bu_phase<RP, STATS>(P, L, st.fb ? P.bm1 : P.bm0, st.fb ? P.bm0 : P.bm1, bu_dynamic(P, st.reached));
+      const int fb = S.st.fb;
+      bu_phase<RP, STATS>(P, L, direct, fb ? P.bm1 : P.bm0, fb ? P.bm0 : P.bm1, bu_dynamic(P, S.st.reached));
     }
     if (!grid_barrier(P, epoch)) return;
-    Slot* nx = &P.ctrl->slot[(L + 1) & 3];
-    const long long nf = (long long)ld_relaxed_u64(&nx->nv);
-    const long long mf = (long long)ld_relaxed_u64(&nx->mf);
-    record_level<STATS>(P, st, nf, converted, t_mark);
-    if (nf == 0) break;
-    st.edges_visited += mf;
-    st.reached += nf;
-    const bool ntd = next_is_top_down(P.policy, P.alpha, P.beta, P.tau_inv, P.script, L + 1, st.td, nf,
-                                      st.nf_cur, mf, P.m - st.edges_visited, P.n);
-    converted = 0;
-    if (st.td && !ntd) {
+    if (threadIdx.x == 0) {
+      LoopState st = S.st;
+      if (st.td) ++S.tdl; else ++S.bul;
+      Slot* nx = &P.ctrl->slot[(L + 1) & 3];
+      const long long nf = (long long)ld_relaxed_u64(&nx->nv);
+      const long long mf = (long long)ld_relaxed_u64(&nx->mf);
+      unsigned long long t_mark = S.t_mark;
+      record_level<STATS>(P, st, nf, S.converted, t_mark);
+      S.t_mark = t_mark;
+      int action = 3;
+      if (nf != 0) {
+        st.edges_visited += mf;
+        st.reached += nf;
+        const bool ntd = next_is_top_down(P.policy, P.alpha, P.beta, P.tau_inv, P.script, L + 1, st.td, nf,
+                                          st.nf_cur, mf, P.m - st.edges_visited, P.n);
+        action = 0;
+        if (st.td && !ntd) {
+          action = 1;
+          st.fb = 0;
+        } else if (!st.td && ntd) {
+          action = 2;
+        } else if (!st.td && !ntd) {
+          st.fb ^= 1;
+        }
+        S.converted = action == 1 || action == 2;
+        if (S.converted) {
+          ++S.conversions;
+          if (STATS && blockIdx.x == 0) P.ctrl->conv_frontier += (unsigned long long)nf;
+        }
+        if (ntd && action == 0) {  // after a conversion they are read once it has run
+          S.items = ld_relaxed_u64(&nx->items);
+          S.mega = ld_relaxed_u64(&nx->mega);
+        }
+        st.td = ntd;
+        st.nf_cur = nf;
+        st.L = L + 1;
+      }
+      S.st = st;
+      S.nf = nf;
+      S.action = action;
+    }
+    __syncthreads();
+    const int action = S.action;
+    if (action == 3) {
+      if (!direct) expand_phase(P);
+      break;
+    }
+    const long long nf = S.nf;
+    if (action == 1) {
       // top-down -> bottom-up: the new frontier's vertex queue becomes bitmap bm0
       zero_words(P.bm0, P.nw);
       if (!grid_barrier(P, epoch)) return;
       scatter_phase(((L + 1) & 1) ? P.qv1 : P.qv0, nf, P.bm0);
       if (!grid_barrier(P, epoch)) return;
-      st.fb = 0;
-      converted = 1;
-    } else if (!st.td && ntd) {
-      // bottom-up -> top-down: work items from the new frontier's vertex queue
-      convert_phase<RP>(P, L, nf);
+    } else if (action == 2) {
+      // bottom-up -> top-down: work items from the new frontier's bitmap
+      convert_phase<RP>(P, L, S.st.fb ? P.bm0 : P.bm1);
       if (!grid_barrier(P, epoch)) return;
-      converted = 1;
-    } else if (!st.td && !ntd) {
-      st.fb ^= 1;
+      if (threadIdx.x == 0) {
+        const Slot* nx = &P.ctrl->slot[(L + 1) & 3];
+        S.items = ld_relaxed_u64(&nx->items);
+        S.mega = ld_relaxed_u64(&nx->mega);
+      }
+      __syncthreads();
     }
-    if (converted) {
-      ++conversions;
-      if (STATS && blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->conv_frontier += (unsigned long long)nf;
-    }
-    if (ntd) {
-      items = ld_relaxed_u64(&nx->items);
-      mega = ld_relaxed_u64(&nx->mega);
-    }
-    st.td = ntd;
-    st.nf_cur = nf;
-    st.L = L + 1;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    P.ctrl->levels = st.L + 1;
-    P.ctrl->td_levels = tdl;
-    P.ctrl->bu_levels = bul;
-    P.ctrl->conversions = conversions;
-    P.ctrl->reached = (unsigned long long)st.reached;
-    P.ctrl->edges_reached = (unsigned long long)st.edges_visited;
+    P.ctrl->levels = S.st.L + 1;
+    P.ctrl->td_levels = S.tdl;
+    P.ctrl->bu_levels = S.bul;
+    P.ctrl->conversions = S.conversions;
+    P.ctrl->reached = (unsigned long long)S.st.reached;
+    P.ctrl->edges_reached = (unsigned long long)S.st.edges_visited;
   }
 }
 
@@ -1049,29 +1226,36 @@ __global__ void __launch_bounds__(1024) k_init_seed(KParams P) {
   if (blockIdx.x == 0 && threadIdx.x == 0) seed_phase<RP>(P);
 }
 
+#ifndef GBFS_KLEVEL_THREADS
+#define GBFS_KLEVEL_THREADS 1024
+#define GBFS_KLEVEL_MINB 1
+#endif
 template <typename RP, bool STATS>
-__global__ void __launch_bounds__(1024) k_level(KParams P, int L, int td, int fb, unsigned long long items,
-                                                unsigned long long mega, long long reached) {
+__global__ void __launch_bounds__(GBFS_KLEVEL_THREADS, GBFS_KLEVEL_MINB) k_level(KParams P, int L, int direct, int td, int fb,
+                                                unsigned long long items, unsigned long long mega,
+                                                long long reached) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Slot* z = &P.ctrl->slot[(L + 2) & 3];
     z->items = 0; z->nv = 0; z->mf = 0; z->nq = 0; z->cursor = 0; z->mega = 0;
   }
   if (td) {
-    td_phase<RP, STATS>(P, L, items, mega);
+    td_phase<RP, STATS>(P, L, direct != 0, items, mega);
   } else {
-    bu_phase<RP, STATS>(P, L, fb ? P.bm1 : P.bm0, fb ? P.bm0 : P.bm1, bu_dynamic(P, reached));
+    bu_phase<RP, STATS>(P, L, direct != 0, fb ? P.bm1 : P.bm0, fb ? P.bm0 : P.bm1, bu_dynamic(P, reached));
   }
 }
 
 __global__ void __launch_bounds__(1024) k_zero_words(unsigned* p, long long nw) { zero_words(p, nw); }
+
+__global__ void __launch_bounds__(1024) k_expand(KParams P) { expand_phase(P); }
 
 __global__ void __launch_bounds__(1024) k_scatter(const int* qv, long long nv, unsigned* bm) {
   scatter_phase(qv, nv, bm);
 }
 
 template <typename RP>
-__global__ void __launch_bounds__(1024) k_convert(KParams P, int L, long long nf) {
-  convert_phase<RP>(P, L, nf);
+__global__ void __launch_bounds__(1024) k_convert(KParams P, int L, const unsigned* fbm) {
+  convert_phase<RP>(P, L, fbm);
 }
 
 template <typename RP, bool STATS>
@@ -1110,6 +1294,7 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
   K.src = src;
   K.init_vis = g->init_vis;
   K.head = g->head;
+  K.lv8 = ws.lv8;
   K.n_live = g->n - g->isolated;
   K.dist = dist;
   K.vis = ws.vis;
@@ -1176,24 +1361,29 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
   int L = 0, fb = 0, tdl = 0, bul = 0, conversions = 0, converted = 0;
   bool td = true;
   Ctrl host_tot{};
+  int direct = K.lv8 == nullptr;
   for (;;) {
-    k_level<RP, STATS><<<grid, block, smem, stream>>>(K, L, td ? 1 : 0, fb, items, mega, reached);
+    if (!direct && L >= 254) {
+      k_expand<<<grid, block, 0, stream>>>(K);
+      direct = 1;
+    }
+    k_level<RP, STATS><<<grid, block, smem, stream>>>(K, L, direct, td ? 1 : 0, fb, items, mega, reached);
     GBFS_CUDA(cudaGetLastError());
     if (td) ++tdl; else ++bul;
     GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,
                               stream));
     GBFS_CUDA(cudaStreamSynchronize(stream));
     const long long nf = (long long)ws.h_slot->nv, mf = (long long)ws.h_slot->mf;
+    if (K.lst && L < K.lst_cap) {
+      bfs_level_stat ls{};
+      GBFS_CUDA(cudaMemcpy(&ls, &K.lst[L], sizeof(ls), cudaMemcpyDeviceToHost));
+      ls.direction = td ? 0 : 1;
+      ls.converted = converted;
+      ls.frontier = nf_cur;
+      ls.found = nf;
+      GBFS_CUDA(cudaMemcpy(&K.lst[L], &ls, sizeof(ls), cudaMemcpyHostToDevice));
+    }
     if (STATS) {
-      if (K.lst && L < K.lst_cap) {
-        bfs_level_stat ls{};
-        GBFS_CUDA(cudaMemcpy(&ls, &K.lst[L], sizeof(ls), cudaMemcpyDeviceToHost));
-        ls.direction = td ? 0 : 1;
-        ls.converted = converted;
-        ls.frontier = nf_cur;
-        ls.found = nf;
-        GBFS_CUDA(cudaMemcpy(&K.lst[L], &ls, sizeof(ls), cudaMemcpyHostToDevice));
-      }
       if (td) host_tot.td_frontier += (unsigned long long)nf_cur; else host_tot.bu_found += (unsigned long long)nf;
     }
     if (nf == 0) break;
@@ -1209,7 +1399,7 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
       fb = 0;
       converted = 1;
     } else if (!td && ntd) {
-      k_convert<RP><<<grid, block, 0, stream>>>(K, L, nf);
+      k_convert<RP><<<grid, block, 0, stream>>>(K, L, fb ? K.bm0 : K.bm1);
       GBFS_CUDA(cudaGetLastError());
       GBFS_CUDA(cudaMemcpyAsync(ws.h_slot, &ws.ctrl->slot[(L + 1) & 3], sizeof(Slot), cudaMemcpyDeviceToHost,
                                 stream));
@@ -1230,6 +1420,8 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
     nf_cur = nf;
     ++L;
   }
+  if (!direct) k_expand<<<grid, block, 0, stream>>>(K);
+  GBFS_CUDA(cudaGetLastError());
   // Write the loop's totals where the persistent kernel would have left them.
   GBFS_CUDA(cudaStreamSynchronize(stream));
   Ctrl c{};
@@ -1317,7 +1509,7 @@ int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_st
   SingleWs& ws = g->ws;
   KParams K;
   fill_kparams(g, src, dist_dev, p, K);
-  const bool stats = st != nullptr || (levels != nullptr && level_cap > 0);
+  const bool stats = st != nullptr;
   if (levels && level_cap > 0) {
     if (ws.lst_cap < level_cap) {
       if (ws.lst) cudaFree(ws.lst);

@@ -209,3 +209,25 @@ def test_degree_ordered_layout(bfs, bits):
     rp, col = G.star_graph(3000)
     check(bfs, rp, col, [0, 5], rp_bits=bits, degree_order=True,
           policies={k: POLICIES[k] for k in ("edges", "bu_from_1")})
+
+
+@pytest.mark.parametrize("launch", [0, 1, 2])
+def test_level_records_without_counters(bfs, launch):
+    """Level records from the non-counting kernel match the counting kernel's (ns aside)."""
+    rp, col = graphgen.rmat(13, seed=21)
+    g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_DEGREE_ORDER)
+    n = len(rp) - 1
+    for src in graphgen.sources(rp, 2, 1010):
+        want = oracle.bfs(rp, col, int(src))
+        d0 = torch.empty(n, dtype=torch.int32, device="cuda")
+        st, lv = bfs.bfs_single_ex(g, int(src), d0, params=bfs.make_params(launch=launch), stats=True, level_cap=64)
+        d1 = torch.empty(n, dtype=torch.int32, device="cuda")
+        none, lv1 = bfs.bfs_single_ex(g, int(src), d1, params=bfs.make_params(launch=launch), level_cap=64)
+        assert none is None
+        assert np.array_equal(d1.cpu().numpy(), want)
+        keys = ("direction", "converted", "frontier", "found")
+        assert [{k: x[k] for k in keys} for x in lv1] == [{k: x[k] for k in keys} for x in lv]
+        assert all(x["edges"] == 0 and x["unvisited"] == 0 for x in lv1)
+        if launch != 1:
+            assert all(x["ns"] > 0 for x in lv1)
+    g.free()
