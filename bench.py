@@ -114,23 +114,37 @@ def harmonic_gteps(edges, seconds):
     return float(len(edges) / np.sum(seconds / edges) / 1e9)
 
 
-def algorithmic_bytes(n, rp_bytes, levels):
-    """Compulsory DRAM bytes of one BFS from its per-level counters.
+def algorithmic_bytes(n, rp_bytes, levels, head=True, queue=True):
+    """Compulsory DRAM bytes of one BFS from its per-level counters, for the
+    library's layout: per-vertex level bytes while the search runs, expanded
+    to int32 distances at the end, and (``head``) the 16-byte head table.
 
-    init 4n + n/8; top-down level: 4|F| + 2*RP*|F| + 4*E_td + 4|F'| (dist)
-    + 4|F'| (queue); bottom-up level: 3n/8 (visited read, next write, visited
-    update) + RP*U + 4*E_bu + 4|F'|; conversion: n/8 + 4|F|.  Random bitmap
-    probes are not counted (the n/8-byte bitmaps fit in half of L2).
+    query: level bytes n + visited init n/8 (read mask) + n/8 (write), final
+    expansion n (read) + 4n (write);
+    top-down level: 8|F| (work items) + 4*E_td (neighbour ids) + per found
+    vertex: head 16 (else 2*RP row pointers) + level byte 1 + work item 8
+    + queue entry 4 (hybrid policies only);
+    bottom-up level: 3n/8 (visited read, next write, visited update) + per
+    unvisited vertex: head 16 + 4 bytes per entry beyond the two the head holds
+    (lower bound 4*max(0, E_bu - 2U)), else RP*U + 4*E_bu; + 1 per found vertex;
+    top-down -> bottom-up conversion: n/8 (zero) + 4|F| (queue);
+    bottom-up -> top-down conversion: n/8 (bitmap) + per vertex head 16 (else
+    2*RP) + work item 8.
+    Random bitmap probes are not counted (the n/8-byte bitmaps and the level
+    bytes are kept in L2).
     """
-    b = 4 * n + n / 8
+    rec = 16 if head else 2 * rp_bytes
+    b = n + n / 4 + 5 * n
     for lv in levels:
         f, e, u, fn = lv["frontier"], lv["edges"], lv["unvisited"], lv["found"]
         if lv["converted"]:
-            b += n / 8 + 4 * f
+            b += n / 8 + (4 * f if lv["direction"] == 1 else (rec + 8) * f)
         if lv["direction"] == 0:
-            b += 4 * f + 2 * rp_bytes * f + 4 * e + 8 * fn
+            b += 8 * f + 4 * e + (rec + 1 + 8 + (4 if queue else 0)) * fn
+        elif head:
+            b += 3 * n / 8 + 16 * u + 4 * max(0, e - 2 * u) + fn
         else:
-            b += 3 * n / 8 + rp_bytes * u + 4 * e + 4 * fn
+            b += 3 * n / 8 + rp_bytes * u + 4 * e + fn
     return b
 
 
@@ -255,6 +269,8 @@ def run_ours(args):
     n, m = len(rp) - 1, len(col)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER))
     params = bfs.make_params(policy=args.policy, launch=args.launch)
+    has_head = m < (1 << 31) - 8  # the library builds the head table when list starts fit int32
+    hybrid = not (args.policy == bfs.BFS_POLICY_TD_ONLY or (args.policy == bfs.BFS_POLICY_AUTO and m < 7 * n))
     stream = torch.cuda.Stream()
     dist_buf = torch.empty(n, dtype=torch.int32, device="cuda")
 
@@ -262,7 +278,8 @@ def run_ours(args):
     per_src = []
     for s in srcs:
         st, lv = bfs.bfs_single_ex(g, int(s), dist_buf, params=params, stats=True, level_cap=1 << 16, stream=stream)
-        per_src.append({"edges": st["edges_reached"] / 2, "bytes": algorithmic_bytes(n, rp_bytes, lv), "stats": st})
+        per_src.append({"edges": st["edges_reached"] / 2, "stats": st,
+                        "bytes": algorithmic_bytes(n, rp_bytes, lv, head=has_head, queue=hybrid)})
 
     def one_step(times):
         for i, s in enumerate(srcs):

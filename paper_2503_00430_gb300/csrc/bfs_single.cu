@@ -67,7 +67,10 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // L2 eviction-priority policies: data read once per level (adjacency, head
 // records) is marked evict-first, the small per-vertex state that every level
@@ -572,7 +575,7 @@ __device__ __forceinline__ bool in_frontier(const unsigned* front, int u) {
 
 // Shared-memory staging of one warp in a bottom-up batch.
 #ifndef GBFS_BU_U
-#define GBFS_BU_U 2
+#define GBFS_BU_U 1
 #endif
 #ifndef GBFS_DRAIN_MIN
 #define GBFS_DRAIN_MIN 32
@@ -580,8 +583,14 @@ __device__ __forceinline__ bool in_frontier(const unsigned* front, int u) {
 constexpr int kBuU = GBFS_BU_U;       // unvisited vertices per lane in flight in a bottom-up round
 constexpr int kDrainMin = GBFS_DRAIN_MIN;  // deferred scans that trigger a drain within a batch
 constexpr int kPendCap = 32 * kBuU + kDrainMin - 1;  // deferred long scans per warp
+#ifndef GBFS_BU_DEPTH
+#define GBFS_BU_DEPTH 2
+#endif
+constexpr int kDepth = GBFS_BU_DEPTH;  // bottom-up rounds whose head records are in flight ahead of use
+constexpr int kNBuf = kDepth + 1;
 struct BuWarpSmem {
-  int4 hbuf[2][32 * kBuU];       // head records of the current and the next round (lane-private slots)
+  int4 hbuf[kNBuf][32 * kBuU];   // head records of the rounds in flight (lane-private slots)
+  int vbuf[kNBuf][32 * kBuU];    // their vertices
   unsigned next[32];             // new-frontier bits of the batch's 32 words
   long long pstart[kPendCap];    // deferred scan: next entry to examine
   int plen[kPendCap];            // entries left
@@ -618,20 +627,21 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
     const int pdeg = have ? sm.pd[j] : 0;
     int ex = have ? sm.pex[j] : 0;
     // Each lane first continues its own vertex for up to bu_thread_max entries,
-    // one aligned 128-bit group (up to four probes in flight) at a time; the
+    // two aligned 128-bit groups (up to eight probes in flight) at a time; the
     // first group masks the entries before ps.
     bool tfound = false;
     for (int done = 0; pl > 0 && done < P.bu_thread_max;) {
       const long long a = ps & ~3ll;
       const int off = (int)(ps - a);
-      const int4 q = __ldg(reinterpret_cast<const int4*>(P.col + a));
-      const int c4[4] = {q.x, q.y, q.z, q.w};
-      bool h[4];
+      const int4 q0 = ldg4_first(P.col + a);
+      const int4 q1 = pl > 4 - off ? ldg4_first(P.col + a + 4) : make_int4(0, 0, 0, 0);
+      const int c8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      bool h[8];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) h[t] = t >= off && t - off < pl && ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u);
+      for (int t = 0; t < 8; ++t) h[t] = t >= off && t - off < pl && ((front[c8[t] >> 5] >> (c8[t] & 31)) & 1u);
       int ft = -1;
 #pragma unroll
-      for (int t = 3; t >= 0; --t)
+      for (int t = 7; t >= 0; --t)
         if (h[t]) ft = t;
       if (ft >= 0) {
         tfound = true;
@@ -639,7 +649,7 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
         pl = 0;
         break;
       }
-      const int step = pl < 4 - off ? pl : 4 - off;
+      const int step = pl < 8 - off ? pl : 8 - off;
       ex += step;
       pl -= step;
       ps += step;
@@ -704,13 +714,25 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
       const long long he = hs + __shfl_sync(kFull, pl, h);
       bool hf = false;
       long long hx = he - hs;
-      for (long long b = hs; b < he; b += 32) {
-        const long long jj = b + lane;
-        const bool hit = jj < he && in_frontier(front, __ldg(P.col + jj));
-        const unsigned bm = __ballot_sync(kFull, hit);
-        if (bm) {
+      // 256 entries per step: two aligned 128-bit loads and eight probes in
+      // flight per lane; the first hit in list order is the warp minimum.
+      for (long long a = hs & ~3ll; a < he; a += 256) {
+        const long long j0 = a + 8 * (long long)lane;
+        int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
+        if (j0 < he) q0 = ldg4_first(P.col + j0);
+        if (j0 + 4 < he) q1 = ldg4_first(P.col + j0 + 4);
+        const int c8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        bool h8[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) h8[t] = j0 + t >= hs && j0 + t < he && in_frontier(front, c8[t]);
+        unsigned first = 0xffffffffu;
+#pragma unroll
+        for (int t = 7; t >= 0; --t)
+          if (h8[t]) first = (unsigned)(j0 + t - hs);
+        const unsigned mn = __reduce_min_sync(kFull, first);
+        if (mn != 0xffffffffu) {
           hf = true;
-          hx = (b - hs) + __ffs(bm);
+          hx = (long long)mn + 1;
           break;
         }
       }
@@ -744,6 +766,33 @@ __device__ __forceinline__ void round_vertices(unsigned act, int excl, int total
   }
 }
 
+// Warp-collective: request the head records of round r of a batch into
+// buffer b (a zero-filled slot for lanes past the end, vertex -1).
+__device__ __forceinline__ void bu_issue_round(const KParams& P, BuWarpSmem& sm, unsigned act, int excl, int total,
+                                               long long w0, int r, int b) {
+  const unsigned lane = lane_id();
+  int v[kBuU];
+  round_vertices(act, excl, total, w0, r * 32 * kBuU, v);
+#pragma unroll
+  for (int k = 0; k < kBuU; ++k) {
+    sm.vbuf[b][32 * k + lane] = v[k];
+    cp_async16_first(&sm.hbuf[b][32 * k + lane], v[k] >= 0 ? P.head + v[k] : P.head, v[k] >= 0 ? 16 : 0);
+  }
+}
+
+// Frontier words holding the two head neighbours of this lane's vertices in
+// round buffer b (0 where a neighbour is missing or the slot is empty).
+__device__ __forceinline__ void bu_probe_words(const BuWarpSmem& sm, const unsigned* front, int b,
+                                               unsigned (&w0)[kBuU], unsigned (&w1)[kBuU]) {
+  const unsigned lane = lane_id();
+#pragma unroll
+  for (int k = 0; k < kBuU; ++k) {
+    const int4 h = sm.vbuf[b][32 * k + lane] >= 0 ? sm.hbuf[b][32 * k + lane] : make_int4(-1, -1, 0, 0);
+    w0[k] = h.x >= 0 ? front[h.x >> 5] : 0u;
+    w1[k] = h.y >= 0 ? front[h.y >> 5] : 0u;
+  }
+}
+
 // One batch of 32 bitmap words (1024 vertices) of a bottom-up level, by one
 // warp.  The unvisited vertices of the batch are packed onto the lanes, two
 // per lane at a time; each looks for a frontier neighbour among the first
@@ -764,41 +813,53 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
   const int total = __shfl_sync(kFull, incl, 31);
   if (STATS) acc.unvisited += (unsigned long long)cnt;
   __syncwarp();
-  int vn[kBuU];
-  if (P.head && total > 0) {
-    // Prologue of the head pipeline: round 0's records are requested now.
-    round_vertices(act, excl, total, w0, 0, vn);
+  const int nrounds = (total + 32 * kBuU - 1) / (32 * kBuU);
+
+  unsigned pw0[kBuU], pw1[kBuU];  // frontier words of the current round's two head neighbours
+  if (P.head) {
+    // Prologue of the head pipeline: the records of rounds 0 .. kDepth-1 are
+    // requested now (one commit group per round, empty past the last round),
+    // then round 0's frontier words.
 #pragma unroll
-    for (int k = 0; k < kBuU; ++k)
-      cp_async16_first(&sm.hbuf[0][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
-    cp_async_commit();
+    for (int r = 0; r < kDepth; ++r) {
+      if (r < nrounds) bu_issue_round(P, sm, act, excl, total, w0, r, r);
+      cp_async_commit();
+    }
+    if (nrounds > 0) {
+      cp_async_wait<kDepth - 1>();
+      bu_probe_words(sm, front, 0, pw0, pw1);
+    }
   }
-  for (int r0 = 0, buf = 0; r0 < total; r0 += 32 * kBuU, buf ^= 1) {
+  for (int r = 0; r < nrounds; ++r) {
+    const int r0 = r * 32 * kBuU;
     int v[kBuU];
     if (P.head) {
       // Head table: the first two neighbours (highest degree first under
       // degree ordering), the list start and the degree in one 16-byte record.
-      // The next round's records are requested before this round's are used,
-      // so a warp keeps one round of head loads in flight while it probes,
-      // marks and drains.  Each lane reads only the slots it filled itself.
-#pragma unroll
-      for (int k = 0; k < kBuU; ++k) v[k] = vn[k];
-      if (r0 + 32 * kBuU < total) {
-        round_vertices(act, excl, total, w0, r0 + 32 * kBuU, vn);
-#pragma unroll
-        for (int k = 0; k < kBuU; ++k)
-          cp_async16_first(&sm.hbuf[buf ^ 1][32 * k + lane], vn[k] >= 0 ? P.head + vn[k] : P.head, vn[k] >= 0 ? 16 : 0);
-      }
+      // Three stages overlap: round r + kDepth's records are requested, round
+      // r + 1's frontier words are loaded, and round r is marked with the
+      // words loaded one round earlier.  Each lane reads only the slots it
+      // filled itself.
+      if (r + kDepth < nrounds) bu_issue_round(P, sm, act, excl, total, w0, r + kDepth, (r + kDepth) % kNBuf);
       cp_async_commit();
-      cp_async_wait1();
+      unsigned nw0[kBuU] = {}, nw1[kBuU] = {};
+      if (r + 1 < nrounds) {
+        cp_async_wait<kDepth - 1>();
+        bu_probe_words(sm, front, (r + 1) % kNBuf, nw0, nw1);
+      }
+      const int buf = r % kNBuf;
+#pragma unroll
+      for (int k = 0; k < kBuU; ++k) v[k] = sm.vbuf[buf][32 * k + lane];
       int4 hd[kBuU];
 #pragma unroll
       for (int k = 0; k < kBuU; ++k) hd[k] = v[k] >= 0 ? sm.hbuf[buf][32 * k + lane] : make_int4(-1, -1, 0, 0);
       unsigned f0[kBuU], f1[kBuU];
 #pragma unroll
       for (int k = 0; k < kBuU; ++k) {
-        f0[k] = hd[k].x >= 0 ? ((front[hd[k].x >> 5] >> (hd[k].x & 31)) & 1u) : 0u;
-        f1[k] = hd[k].y >= 0 ? ((front[hd[k].y >> 5] >> (hd[k].y & 31)) & 1u) : 0u;
+        f0[k] = hd[k].x >= 0 ? ((pw0[k] >> (hd[k].x & 31)) & 1u) : 0u;
+        f1[k] = hd[k].y >= 0 ? ((pw1[k] >> (hd[k].y & 31)) & 1u) : 0u;
+        pw0[k] = nw0[k];
+        pw1[k] = nw1[k];
       }
 #pragma unroll
       for (int k = 0; k < kBuU; ++k) {
