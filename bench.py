@@ -48,8 +48,9 @@ def peaks():
 
 
 def measured_traffic():
-    """Per-launch DRAM traffic of the persistent kernel from the committed ncu
-    record, or None when the kernel's sources changed since it was captured."""
+    """(mean per-launch DRAM traffic, indices of the captured sources) of the
+    persistent kernel from the committed ncu record, or None when the kernel's
+    sources changed since it was captured."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "bfs_persistent_traffic.json")) as f:
@@ -60,7 +61,7 @@ def measured_traffic():
                 h.update(f.read())
         if h.hexdigest() != rec["source_sha256"]:
             return None
-        return float(rec["traffic_bytes_per_launch_s25"])
+        return float(rec["traffic_bytes_per_launch_s25"]), list(rec.get("source_indices", []))
     except Exception:
         return None
 
@@ -318,6 +319,17 @@ def run_ours(args):
     lat = np.array(secs) * 1e3
     hbm, peak_kind = peaks()
     achieved = float(np.sum(byts) / np.sum(secs) / 1e9)
+    # DRAM traffic of the same kernel from the committed ncu record (captured on
+    # this workload), and its ratio to the algorithmic bytes of the captured sources.
+    traffic, traffic_ratio = None, None
+    default_run = (args.scale == SCALE and args.workload == "rmat25" and not args.no_degree_order
+                   and args.policy == 0 and args.launch == 0)
+    mt = measured_traffic() if default_run else None
+    if mt is not None:
+        traffic = mt[0]
+        idx = [i for i in mt[1] if i < len(per_src)]
+        if idx:
+            traffic_ratio = traffic / float(np.mean([per_src[i]["bytes"] for i in idx]))
 
     # End to end through the C ABI with a pinned host output buffer (D2H copy inside).
     host_out = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
@@ -354,7 +366,8 @@ def run_ours(args):
                     "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "peak_kind": peak_kind,
-                     "traffic": measured_traffic() if (args.scale == SCALE and args.workload == "rmat25") else None,
+                     "traffic": traffic,
+                     "traffic_vs_algorithmic": traffic_ratio,
                      "kernel": "bfs_persistent_kernel<long long,false> (one launch per BFS)",
                      "bytes_per_bfs_mean": float(np.mean([p["bytes"] for p in per_src]))},
         "e2e": e2e,
