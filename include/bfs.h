@@ -120,7 +120,12 @@ typedef struct bfs_params {
                                 whole warp (default 256) */
     int32_t ms_degree_order; /* bfs_multi pull levels visit vertices by decreasing degree (1, default)
                                 or by id (0) */
-    int32_t reserved[3];
+    int32_t ms_alpha;        /* bfs_multi: a push level is followed by a pull level when
+                                ms_alpha * (degree sum of the new frontier) > entries of vertices not
+                                yet reached by every lane (default 2: a pull level scans those lists
+                                nearly in full while lanes remain, unlike a single-source bottom-up
+                                level, so it needs a denser frontier than alpha asks for) */
+    int32_t reserved[2];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique

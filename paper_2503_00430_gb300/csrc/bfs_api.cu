@@ -254,6 +254,7 @@ static int check_params(const bfs_params& p) {
   if (p.bu_thread_max < 0 || p.bu_thread_max > (1 << 20)) return BFS_EINVAL;
   if (p.ms_lanes < 1 || p.ms_lanes > 256 || p.ms_ring < 2 || p.ms_ring > 8 || p.ms_heavy_min < 0) return BFS_EINVAL;
   if (p.ms_degree_order < 0 || p.ms_degree_order > 1) return BFS_EINVAL;
+  if (p.ms_alpha < 1) return BFS_EINVAL;
   return BFS_OK;
 }
 
@@ -302,6 +303,7 @@ void bfs_params_default(bfs_params* p) {
   p->ms_ring = 8;
   p->ms_heavy_min = 256;
   p->ms_degree_order = 1;
+  p->ms_alpha = 2;
 }
 
 int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n, int64_t m,

@@ -72,6 +72,9 @@ struct MultiWs {
 namespace {
 
 constexpr int kMsMaxRing = 8;
+#ifndef GBFS_MS_PULL_MINB
+#define GBFS_MS_PULL_MINB 3  // pull kernels: blocks of 256 per SM the register budget must allow
+#endif
 
 __device__ __forceinline__ unsigned ms_lane() { return threadIdx.x & 31u; }
 
@@ -97,6 +100,23 @@ __device__ __forceinline__ Mask<W> load_mask(const unsigned long long* p) {
     m.w[0] = a.x; m.w[1] = a.y;
   } else {
     m.w[0] = p[0];
+  }
+  return m;
+}
+
+// Read-only gather of a frontier mask (the array was written by an earlier launch).
+template <int W>
+__device__ __forceinline__ Mask<W> ldg_mask(const unsigned long long* p) {
+  Mask<W> m;
+  if constexpr (W == 4) {
+    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+    const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+    m.w[0] = a.x; m.w[1] = a.y; m.w[2] = b.x; m.w[3] = b.y;
+  } else if constexpr (W == 2) {
+    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+    m.w[0] = a.x; m.w[1] = a.y;
+  } else {
+    m.w[0] = __ldg(p);
   }
   return m;
 }
@@ -132,6 +152,8 @@ struct MsArgs {
   const int* order;
   MsCtrl* ctrl;
   int heavy_min;               // pull: vertices with more entries go to the warp-cooperative pass
+  int dense;                   // push: no touched list; the apply pass scans every vertex
+  int want_queue;              // pull / dense apply: also append the new frontier's vertices to qnext
 };
 
 template <int W>
@@ -200,40 +222,116 @@ __global__ void k_ms_seed(MsArgs A, const int* src, int lanes) {
   }
 }
 
-// ---- push: warp per frontier vertex, OR its new lanes into neighbours' accumulators ----
-template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const unsigned lane = ms_lane();
-  unsigned long long edges = 0;
-  for (long long qi = gw; qi < nq; qi += nwarps) {
-    const int u = A.qcur[qi];
-    const Mask<W> f = load_mask<W>(A.Fcur + (long long)u * W);
-    const long long s = rpv<RP>(A.rp, u), e = rpv<RP>(A.rp, (long long)u + 1);
-    if (lane == 0) edges += (unsigned long long)(e - s);
-    for (long long j0 = s; j0 < e; j0 += 32) {
-      const long long j = j0 + lane;
-      bool touch = false;
-      int v = 0;
-      if (j < e) {
-        v = __ldg(A.col + j);
-        const Mask<W> x = load_mask<W>(A.X + (long long)v * W);
-        bool any = false;
+// ---- push: frontier vertices OR their new lanes into neighbours' accumulators ----
+// Vertices with more than kMsPushChunk entries are cut into chunks handed out
+// as tickets (records planned first), so a hub's list is pushed by many warps.
+constexpr int kMsPushChunk = 256;
+
+// Plan: one record per frontier vertex with more than kMsPushChunk entries;
+// one packed atomic per warp hands out record slots and chunk tickets in order.
+template <typename RP>
+__global__ void __launch_bounds__(256) k_ms_push_plan(MsArgs A, long long nq) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long base = tid - (tid & 31); base < nq; base += nth) {
+    const long long i = base + ms_lane();
+    long long s = 0, d = 0;
+    int u = 0;
+    if (i < nq) {
+      u = A.qcur[i];
+      s = rpv<RP>(A.rp, u);
+      d = rpv<RP>(A.rp, (long long)u + 1) - s;
+    }
+    const bool big = d > kMsPushChunk;
+    const int nch = big ? (int)((d + kMsPushChunk - 1) / kMsPushChunk) : 0;
+    const unsigned bm = __ballot_sync(0xffffffffu, big);
+    if (!bm) continue;
+    int incl = nch;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          const unsigned long long add = f.w[k] & ~x.w[k];
-          if (add) {
-            atomicOr(A.acc + (long long)v * W + k, add);
-            any = true;
-          }
-        }
-        if (any) {
-          const unsigned bit = 1u << (v & 31);
-          touch = !(atomicOr(A.touched_bm + (v >> 5), bit) & bit);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)ms_lane() >= o) incl += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long b = 0;
+    if (ms_lane() == 31)
+      b = atomicAdd(&A.ctrl->nheavy, (unsigned long long)__popc(bm) | ((unsigned long long)tot << kMsCountBits));
+    b = __shfl_sync(0xffffffffu, b, 31);
+    if (big) {
+      unsigned lt;
+      asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+      MsHeavy& r = A.heavy[(b & ((1ull << kMsCountBits) - 1)) + __popc(bm & lt)];
+      r.start = s;
+      r.deg = d;
+      r.base = (b >> kMsCountBits) + (unsigned long long)(incl - nch);
+      r.v = u;
+    }
+  }
+}
+
+// Warp-collective: push the lanes f of one vertex along entries [s, e), 32 per step.
+template <int W>
+__device__ __forceinline__ void ms_push_span(const MsArgs& A, const Mask<W>& f, long long s, long long e) {
+  const unsigned lane = ms_lane();
+  for (long long j0 = s; j0 < e; j0 += 32) {
+    const long long j = j0 + lane;
+    bool touch = false;
+    int v = 0;
+    if (j < e) {
+      v = __ldg(A.col + j);
+      const Mask<W> x = load_mask<W>(A.X + (long long)v * W);
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const unsigned long long add = f.w[k] & ~x.w[k];
+        if (add) {
+          atomicOr(A.acc + (long long)v * W + k, add);
+          any = true;
         }
       }
-      warp_append(touch, v, &A.ctrl->ntouch, A.touched);
+      if (any && !A.dense) {
+        const unsigned bit = 1u << (v & 31);
+        touch = !(atomicOr(A.touched_bm + (v >> 5), bit) & bit);
+      }
+    }
+    if (!A.dense) warp_append(touch, v, &A.ctrl->ntouch, A.touched);
+  }
+}
+
+// Warp per frontier vertex of at most kMsPushChunk entries, then warp per chunk
+// ticket of the planned vertices (ticket t belongs to the last record whose
+// base is <= t: 32-way search).
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
+  const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned lane = ms_lane();
+  const unsigned long long hv = A.ctrl->nheavy;  // written by k_ms_push_plan earlier on this stream
+  const long long nrec = (long long)(hv & ((1ull << kMsCountBits) - 1)), nch = (long long)(hv >> kMsCountBits);
+  unsigned long long edges = 0;
+  for (long long u0 = gw; u0 < nq + nch; u0 += nwarps) {
+    if (u0 < nq) {
+      const int u = A.qcur[u0];
+      const long long s = rpv<RP>(A.rp, u), e = rpv<RP>(A.rp, (long long)u + 1);
+      if (e - s > kMsPushChunk) continue;  // pushed by chunk tickets
+      if (lane == 0) edges += (unsigned long long)(e - s);
+      ms_push_span<W>(A, load_mask<W>(A.Fcur + (long long)u * W), s, e);
+    } else {
+      const long long t = u0 - nq;
+      long long lo = 0, hi = nrec;
+      while (hi - lo > 1) {
+        const long long step = (hi - lo + 31) / 32;
+        const long long idx = lo + (long long)lane * step;
+        const bool ok = idx < hi && (long long)A.heavy[idx].base <= t;
+        const unsigned bm = __ballot_sync(0xffffffffu, ok);
+        lo += (long long)(31 - __clz(bm)) * step;
+        hi = lo + step < hi ? lo + step : hi;
+      }
+      const MsHeavy r = A.heavy[lo];
+      const long long cs = r.start + (t - (long long)r.base) * kMsPushChunk;
+      const long long ce = cs + (r.deg - (cs - r.start) < kMsPushChunk ? r.deg - (cs - r.start) : kMsPushChunk);
+      if (lane == 0) edges += (unsigned long long)(ce - cs);
+      ms_push_span<W>(A, load_mask<W>(A.Fcur + r.v * W), cs, ce);
     }
   }
   if (lane == 0 && edges) atomicAdd(&A.ctrl->edges, edges);
@@ -246,6 +344,9 @@ __global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long nf = 0, mf = 0, dd = 0;
+  Mask<W> act_acc;
+#pragma unroll
+  for (int k = 0; k < W; ++k) act_acc.w[k] = 0;
   for (long long base = tid - (tid & 31); base < nt; base += nth) {
     const long long i = base + ms_lane();
     bool in = i < nt;
@@ -278,8 +379,10 @@ __global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
       }
     }
     warp_append(nz, v, &A.ctrl->nq, A.qnext);
-    warp_or_active<W>(nn, A.ctrl);
+#pragma unroll
+    for (int k = 0; k < W; ++k) act_acc.w[k] |= nn.w[k];
   }
+  warp_or_active<W>(act_acc, A.ctrl);
   nf = warp_sum(nf);
   mf = warp_sum(mf);
   dd = warp_sum(dd);
@@ -290,12 +393,81 @@ __global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
   }
 }
 
+// ---- apply after a dense push: every vertex, in id order (coalesced) ----
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_apply_dense(MsArgs A) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  unsigned long long nf = 0, mf = 0, dd = 0;
+  Mask<W> act_acc;
+#pragma unroll
+  for (int k = 0; k < W; ++k) act_acc.w[k] = 0;
+  for (long long base = tid - (tid & 31); base < A.n; base += nth) {
+    const long long v = base + ms_lane();
+    bool nz = false;
+    Mask<W> nn;
+#pragma unroll
+    for (int k = 0; k < W; ++k) nn.w[k] = 0;
+    if (v < A.n) {
+      const Mask<W> a = load_mask<W>(A.acc + v * W);
+      if (!is_zero<W>(a)) {
+        Mask<W> x = load_mask<W>(A.X + v * W);
+        Mask<W> z;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          nn.w[k] = a.w[k] & ~x.w[k];
+          x.w[k] |= nn.w[k];
+          z.w[k] = 0;
+        }
+        store_mask<W>(A.acc + v * W, z);
+        nz = !is_zero<W>(nn);
+        if (nz) {
+          store_mask<W>(A.X + v * W, x);
+          store_mask<W>(A.Fnext + v * W, nn);  // Fnext was zeroed before the push
+          const long long d = rpv<RP>(A.rp, v + 1) - rpv<RP>(A.rp, v);
+          nf += 1;
+          mf += (unsigned long long)d;
+          if (is_full<W>(x, A.full)) dd += (unsigned long long)d;
+        }
+      }
+    }
+    if (A.want_queue) warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
+#pragma unroll
+    for (int k = 0; k < W; ++k) act_acc.w[k] |= nn.w[k];
+  }
+  warp_or_active<W>(act_acc, A.ctrl);
+  nf = warp_sum(nf);
+  mf = warp_sum(mf);
+  dd = warp_sum(dd);
+  if (ms_lane() == 0) {
+    if (nf) atomicAdd(&A.ctrl->nf, nf);
+    if (mf) atomicAdd(&A.ctrl->mf, mf);
+    if (dd) atomicAdd(&A.ctrl->done_deg, dd);
+  }
+}
+
+// ---- frontier queue from the frontier masks (before a push level that follows
+// a level which kept no queue) ----
+template <int W>
+__global__ void __launch_bounds__(256) k_ms_compact(MsArgs A) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long base = tid - (tid & 31); base < A.n; base += nth) {
+    const long long v = base + ms_lane();
+    const bool nz = v < A.n && !is_zero<W>(load_mask<W>(A.Fcur + v * W));
+    warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
+  }
+}
+
 // ---- pull: thread per vertex; high-degree vertices deferred to the warp pass ----
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
+__global__ void __launch_bounds__(256, GBFS_MS_PULL_MINB) k_ms_pull(MsArgs A) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long nf = 0, mf = 0, dd = 0, edges = 0;
+  Mask<W> act_acc;
+#pragma unroll
+  for (int k = 0; k < W; ++k) act_acc.w[k] = 0;
   for (long long base = tid - (tid & 31); base < A.n; base += nth) {
     const long long oi = base + ms_lane();
     const long long v = (A.order && oi < A.n) ? (long long)A.order[oi] : oi;
@@ -317,16 +489,19 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
 #pragma unroll
           for (int k = 0; k < W; ++k) acc.w[k] = x.w[k];
           // Aligned groups of four entries: one 128-bit load, then the four
-          // neighbours' masks are gathered together before they are combined.
+          // neighbours' masks are gathered together before they are combined;
+          // the next group's entries are requested before this group's masks.
           long long j0 = s & ~3ll;
+          int4 q = __ldg(reinterpret_cast<const int4*>(A.col + j0));
           for (; j0 < e; j0 += 4) {
-            const int4 q = __ldg(reinterpret_cast<const int4*>(A.col + j0));
+            const int4 qn = j0 + 4 < e ? __ldg(reinterpret_cast<const int4*>(A.col + j0 + 4)) : make_int4(0, 0, 0, 0);
             const int c4[4] = {q.x, q.y, q.z, q.w};
+            q = qn;
             Mask<W> f[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
               if (j0 + t >= s && j0 + t < e) {
-                f[t] = load_mask<W>(A.Fcur + (long long)c4[t] * W);
+                f[t] = ldg_mask<W>(A.Fcur + (long long)c4[t] * W);
               } else {
 #pragma unroll
                 for (int k = 0; k < W; ++k) f[t].w[k] = 0;
@@ -356,7 +531,7 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
       }
       if (!defer) store_mask<W>(A.Fnext + v * W, nn);
     }
-    warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
+    if (A.want_queue) warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
     {
       // Deferred vertices: one record each; one packed atomic per warp hands
       // out record slots and chunk tickets in the same order.
@@ -385,8 +560,10 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
         }
       }
     }
-    warp_or_active<W>(nn, A.ctrl);
+#pragma unroll
+    for (int k = 0; k < W; ++k) act_acc.w[k] |= nn.w[k];
   }
+  warp_or_active<W>(act_acc, A.ctrl);
   nf = warp_sum(nf);
   mf = warp_sum(mf);
   dd = warp_sum(dd);
@@ -405,7 +582,7 @@ __global__ void __launch_bounds__(256) k_ms_pull(MsArgs A) {
 // (four gathers in flight per lane), stops once the vertex's pending active
 // lanes are all covered, and ORs the new lanes into the vertex's accumulator.
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_heavy_chunks(MsArgs A) {
+__global__ void __launch_bounds__(256, GBFS_MS_PULL_MINB) k_ms_heavy_chunks(MsArgs A) {
   const unsigned long long hv = A.ctrl->nheavy;  // written by k_ms_pull earlier on this stream
   const long long nrec = (long long)(hv & ((1ull << kMsCountBits) - 1)), nch = (long long)(hv >> kMsCountBits);
   const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
@@ -430,39 +607,53 @@ __global__ void __launch_bounds__(256) k_ms_heavy_chunks(MsArgs A) {
 #pragma unroll
     for (int k = 0; k < W; ++k) have.w[k] |= x.w[k];
     if (covers<W>(have, A.act)) continue;
-    Mask<W> acc;
+    // Lane-local OR over the chunk; the warp combines the lanes (and tests
+    // whether the vertex's pending lanes are covered) every fourth step.  The
+    // next step's entries are requested before this step's masks.
+    Mask<W> la;
 #pragma unroll
-    for (int k = 0; k < W; ++k) acc.w[k] = 0;
+    for (int k = 0; k < W; ++k) la.w[k] = 0;
     long long base = cs & ~3ll;
-    for (; base < ce; base += 128) {
+    int4 q = base + 4 * (long long)lane < ce ? __ldg(reinterpret_cast<const int4*>(A.col + base + 4 * lane))
+                                            : make_int4(0, 0, 0, 0);
+    for (int step = 1; base < ce; base += 128, ++step) {
       const long long j = base + 4 * (long long)lane;
-      int4 q = make_int4(0, 0, 0, 0);
-      if (j < ce) q = __ldg(reinterpret_cast<const int4*>(A.col + j));
       const int c4[4] = {q.x, q.y, q.z, q.w};
+      q = j + 128 < ce ? __ldg(reinterpret_cast<const int4*>(A.col + j + 128)) : make_int4(0, 0, 0, 0);
       Mask<W> f[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (j + u >= cs && j + u < ce) {
-          f[u] = load_mask<W>(A.Fcur + (long long)c4[u] * W);
+          f[u] = ldg_mask<W>(A.Fcur + (long long)c4[u] * W);
         } else {
 #pragma unroll
           for (int k = 0; k < W; ++k) f[u].w[k] = 0;
         }
       }
 #pragma unroll
-      for (int k = 0; k < W; ++k) {
-        unsigned long long o = f[0].w[k] | f[1].w[k] | f[2].w[k] | f[3].w[k];
+      for (int k = 0; k < W; ++k) la.w[k] |= f[0].w[k] | f[1].w[k] | f[2].w[k] | f[3].w[k];
+      if ((step & 3) == 0) {
+        Mask<W> tot;
 #pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) o |= __shfl_xor_sync(0xffffffffu, o, sh);
-        acc.w[k] |= o;
-      }
-      Mask<W> tot;
+        for (int k = 0; k < W; ++k) {
+          unsigned long long o = la.w[k];
 #pragma unroll
-      for (int k = 0; k < W; ++k) tot.w[k] = acc.w[k] | have.w[k];
-      if (covers<W>(tot, A.act)) {
-        base += 128;
-        break;
+          for (int sh = 16; sh > 0; sh >>= 1) o |= __shfl_xor_sync(0xffffffffu, o, sh);
+          tot.w[k] = o | have.w[k];
+        }
+        if (covers<W>(tot, A.act)) {
+          base += 128;
+          break;
+        }
       }
+    }
+    Mask<W> acc;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      unsigned long long o = la.w[k];
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) o |= __shfl_xor_sync(0xffffffffu, o, sh);
+      acc.w[k] = o;
     }
     if (lane == 0) {
       edges += (unsigned long long)((base < ce ? base : ce) - cs);
@@ -483,6 +674,9 @@ __global__ void __launch_bounds__(256) k_ms_heavy_apply(MsArgs A) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long nf = 0, mf = 0, dd = 0;
+  Mask<W> act_acc;
+#pragma unroll
+  for (int k = 0; k < W; ++k) act_acc.w[k] = 0;
   for (long long base = tid - (tid & 31); base < nrec; base += nth) {
     const long long i = base + ms_lane();
     bool nz = false;
@@ -512,9 +706,11 @@ __global__ void __launch_bounds__(256) k_ms_heavy_apply(MsArgs A) {
         if (is_full<W>(x, A.full)) dd += (unsigned long long)r.deg;
       }
     }
-    warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
-    warp_or_active<W>(nn, A.ctrl);
+    if (A.want_queue) warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
+#pragma unroll
+    for (int k = 0; k < W; ++k) act_acc.w[k] |= nn.w[k];
   }
+  warp_or_active<W>(act_acc, A.ctrl);
   nf = warp_sum(nf);
   mf = warp_sum(mf);
   dd = warp_sum(dd);
@@ -531,17 +727,17 @@ __global__ void k_ms_zero(unsigned long long* p, long long count) {
   for (long long i = tid; i < count; i += nth) p[i] = 0ull;
 }
 
-// ---- writer: ring levels [l0, l0 + nlev) into dist[row0 + i][v] ----
-// One block per tile of 32 vertices at a time: the tile's masks for all the
-// window's levels are staged in shared memory; thread i handles lane i and
-// writes that lane's 32 distances as one 32-byte (uint8) or 128-byte (int32)
-// run of its output row.  The first window also writes the "unreached" value
-// for lanes not found in it; later windows write only what they found.
-// Tile of kWt vertices: per (word, vertex) the lanes found in the window and
-// the three bits of the finding level's offset (bit-sliced over 64 lanes) go
-// to shared memory, vertex index innermost; then each warp writes one output
-// row segment at a time, lane j covering vertices j, j+32, j+64, j+96, so
-// every store instruction covers consecutive vertices of one row.
+// ---- writer: ring levels [l0, l0 + nlev) into dist[i][v] ----
+// A block owns a tile of 128 vertices.  Phase 1 (coalesced reads of the ring):
+// per (vertex, word) the lanes found in the window and the three bits of the
+// finding level's offset, bit-sliced over 64 lanes, go to shared memory.
+// Phase 2: each warp takes one word and a share of its 64 rows; each lane
+// loads the four planes of its four consecutive vertices once into registers
+// and, row by row, extracts its four entries, so the warp stores 128
+// consecutive entries of the row with one vector store per lane (4 bytes for
+// uint8, 16 for int32).  The first window writes every entry ("unreached"
+// where the lane was not found); later windows write only what they found and
+// skip rows with nothing found in the tile.
 constexpr int kWt = 128;
 
 template <int W, typename T>
@@ -551,19 +747,22 @@ __global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, l
   __shared__ unsigned long long tile_or[W];
   const long long ntiles = (n + kWt - 1) / kWt;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int wpw = (int)nwarp / W;                 // warps per word
+  const int w = (int)warp % W, part = (int)warp / W;
+  const int rows_per = (64 + wpw - 1) / wpw;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long v0 = tile * kWt;
     if (threadIdx.x < W) tile_or[threadIdx.x] = 0ull;
     __syncthreads();
     for (int idx = threadIdx.x; idx < kWt * W; idx += blockDim.x) {
-      const int j = idx / W, w = idx % W;
+      const int j = idx / W, ww = idx % W;
       const long long v = v0 + j;
       unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0;
       if (v < n) {
         unsigned long long m[kMsMaxRing];
 #pragma unroll
         for (int l = 0; l < kMsMaxRing; ++l)
-          m[l] = l < nlev ? F[(long long)((l0 + l) % ring) * n * W + v * W + w] : 0ull;
+          m[l] = l < nlev ? F[(long long)((l0 + l) % ring) * n * W + v * W + ww] : 0ull;
 #pragma unroll
         for (int l = kMsMaxRing - 1; l >= 0; --l) {
           f |= m[l];
@@ -572,28 +771,50 @@ __global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, l
           p2 = (p2 & ~m[l]) | ((l & 4) ? m[l] : 0ull);
         }
       }
-      pl[0][w][j] = f;
-      pl[1][w][j] = p0;
-      pl[2][w][j] = p1;
-      pl[3][w][j] = p2;
-      if (!first && f) atomicOr(&tile_or[w], f);
+      pl[0][ww][j] = f;
+      pl[1][ww][j] = p0;
+      pl[2][ww][j] = p1;
+      pl[3][ww][j] = p2;
+      if (!first && f) atomicOr(&tile_or[ww], f);
     }
     __syncthreads();
-    for (int i = (int)warp; i < lanes; i += (int)nwarp) {
-      const int w = i >> 6, b = i & 63;
-      if (!first && !((tile_or[w] >> b) & 1ull)) continue;
-      T* row = dist + (long long)i * n + v0;
+    if ((int)warp < wpw * W) {
+      const int j0 = 4 * (int)lane;
+      unsigned long long f[4], q0[4], q1[4], q2[4];
 #pragma unroll
-      for (int r = 0; r < kWt / 32; ++r) {
-        const int j = (int)lane + 32 * r;
-        if (v0 + j >= n) break;
-        const bool fnd = (pl[0][w][j] >> b) & 1ull;
-        if (fnd) {
-          const int lv = (int)(((pl[1][w][j] >> b) & 1ull) | (((pl[2][w][j] >> b) & 1ull) << 1) |
-                               (((pl[3][w][j] >> b) & 1ull) << 2));
-          row[j] = (T)(l0 + lv);
-        } else if (first) {
-          row[j] = unreached;
+      for (int t = 0; t < 4; ++t) {
+        f[t] = pl[0][w][j0 + t];
+        q0[t] = pl[1][w][j0 + t];
+        q1[t] = pl[2][w][j0 + t];
+        q2[t] = pl[3][w][j0 + t];
+      }
+      const long long va = v0 + j0;
+      const bool full_tile = v0 + kWt <= n;
+      const int b0 = part * rows_per, b1 = min(64, b0 + rows_per);
+      for (int b = b0; b < b1; ++b) {
+        const int i = 64 * w + b;
+        if (i >= lanes) break;
+        if (!first && !((tile_or[w] >> b) & 1ull)) continue;
+        T* row = dist + (long long)i * n + va;
+        T val[4];
+        bool fnd[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          fnd[t] = (f[t] >> b) & 1ull;
+          const int lv = (int)(((q0[t] >> b) & 1ull) | (((q1[t] >> b) & 1ull) << 1) | (((q2[t] >> b) & 1ull) << 2));
+          val[t] = fnd[t] ? (T)(l0 + lv) : unreached;
+        }
+        if (first && full_tile && (reinterpret_cast<uintptr_t>(row) % (4 * sizeof(T))) == 0) {
+          if constexpr (sizeof(T) == 1) {
+            *reinterpret_cast<uchar4*>(row) = make_uchar4((unsigned char)val[0], (unsigned char)val[1],
+                                                          (unsigned char)val[2], (unsigned char)val[3]);
+          } else {
+            *reinterpret_cast<int4*>(row) = make_int4((int)val[0], (int)val[1], (int)val[2], (int)val[3]);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (va + t < n && (first || fnd[t])) row[t] = val[t];
         }
       }
     }
@@ -667,14 +888,19 @@ namespace {
 
 // One level of a lane group, launched asynchronously: every count a later
 // kernel needs is read from the control block on the device.
+// A push level whose frontier's degree sum exceeds n / 8 touches a large share
+// of the vertices: it keeps no touched list and applies by a scan of all vertices.
 template <int W, typename RP>
-void ms_step(const MsArgs& A, bool push, long long nf, unsigned long long* Fn, long long n, int grid,
+void ms_step(MsArgs A, bool push, bool dense, long long nf, unsigned long long* Fn, long long n, int grid,
              cudaStream_t s) {
   cudaMemsetAsync(A.ctrl, 0, sizeof(MsCtrl), s);
+  A.dense = push && dense ? 1 : 0;
   if (push) {
     k_ms_zero<<<grid, 256, 0, s>>>(Fn, n * W);
+    k_ms_push_plan<RP><<<grid, 256, 0, s>>>(A, nf);
     k_ms_push<W, RP><<<grid, 256, 0, s>>>(A, nf);
-    k_ms_apply<W, RP><<<grid, 256, 0, s>>>(A);
+    if (A.dense) k_ms_apply_dense<W, RP><<<grid, 256, 0, s>>>(A);
+    else k_ms_apply<W, RP><<<grid, 256, 0, s>>>(A);
   } else {
     k_ms_pull<W, RP><<<grid, 256, 0, s>>>(A);
     k_ms_heavy_chunks<W, RP><<<grid, 256, 0, s>>>(A);
@@ -706,6 +932,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   A.ctrl = ws.ctrl;
   A.heavy_min = p.ms_heavy_min;
   A.order = p.ms_degree_order ? ws.order : nullptr;
+  A.want_queue = 0;
   const int K = ws.ring;
   auto slot = [&](int l) { return ws.F + (long long)(l % K) * n * W; };
   // Unique sources form the level-0 frontier queue.
@@ -725,6 +952,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   long long nf = (long long)uniq.size(), mf = (long long)ws.h_ctrl->mf, nf_prev = nf;
   long long m_unfinished = g->m;
   bool push = true;
+  bool queue_ready = true;  // ws.q[qc] lists the current frontier (pull and dense push levels keep none)
   int L = 0, flushed = 0, qc = 0;
   bool first_flush = true;
   int rc = BFS_OK;
@@ -741,7 +969,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   for (;;) {
     // Direction for this level (edge-count rule, Section 2's BFS-Hybrid-dagger).
     if (L > 0) {
-      if (push) push = !((long long)p.alpha * mf > m_unfinished);
+      if (push) push = !((long long)p.ms_alpha * mf > m_unfinished);
       else push = (long long)p.beta * nf < n && nf < nf_prev;
     }
     if (L + 1 - flushed >= K) {
@@ -750,10 +978,19 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
     }
     unsigned long long* Fn = slot(L + 1);
     A.Fcur = slot(L);
+    if (push && !queue_ready) {
+      MsArgs C = A;
+      C.qnext = ws.q[qc];
+      GBFS_CUDA(cudaMemsetAsync(&ws.ctrl->nq, 0, sizeof(unsigned long long), s));
+      k_ms_compact<W><<<grid, block, 0, s>>>(C);
+      GBFS_CUDA(cudaGetLastError());
+    }
     A.Fnext = Fn;
     A.qcur = ws.q[qc];
     A.qnext = ws.q[qc ^ 1];
-    ms_step<W, RP>(A, push, nf, Fn, n, grid, s);
+    const bool dense = mf > n / 8;
+    ms_step<W, RP>(A, push, dense, nf, Fn, n, grid, s);
+    queue_ready = push && !dense;
     GBFS_CUDA(cudaGetLastError());
     GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
     GBFS_CUDA(cudaStreamSynchronize(s));
@@ -981,7 +1218,8 @@ void serve_step(ServeGroup* G, bool push) {
   A.order = G->order;
   A.ctrl = G->ctrl;
   A.heavy_min = G->heavy_min;
-  ms_step<1, RP>(A, push, G->nf, A.Fnext, G->n, G->g->num_sms * 8, G->stream);
+  A.want_queue = 1;
+  ms_step<1, RP>(A, push, false, G->nf, A.Fnext, G->n, G->g->num_sms * 8, G->stream);
 }
 
 int serve_flush(ServeGroup* G, int upto) {
