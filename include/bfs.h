@@ -114,8 +114,8 @@ typedef struct bfs_params {
                                 its own lane for up to this many more entries before the warp takes
                                 over (default 32) */
     int32_t ms_lanes;        /* bfs_multi: sources per group (1..256, default 256) */
-    int32_t ms_ring;         /* bfs_multi: frontier levels kept before they are written out (2..8,
-                                default 8) */
+    int32_t ms_ring;         /* bfs_multi: frontier levels kept before they are written out (2..16,
+                                default 16) */
     int32_t ms_heavy_min;    /* bfs_multi pull levels: vertices with more entries are scanned by a
                                 whole warp (default 256) */
     int32_t ms_degree_order; /* bfs_multi pull levels visit vertices by decreasing degree (1, default)
@@ -125,7 +125,11 @@ typedef struct bfs_params {
                                 yet reached by every lane (default 2: a pull level scans those lists
                                 nearly in full while lanes remain, unlike a single-source bottom-up
                                 level, so it needs a denser frontier than alpha asks for) */
-    int32_t reserved[2];
+    int32_t ms_relabel;      /* bfs_multi: run on a copy of the graph whose vertices are renumbered by
+                                decreasing degree (1, default; built once per graph on first use and
+                                kept until bfs_graph_free: 4m + 8n bytes plus the row pointers), so the
+                                masks most lists point to share cache lines; 0 = the graph as uploaded */
+    int32_t reserved[1];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique

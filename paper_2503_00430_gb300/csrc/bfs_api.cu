@@ -160,6 +160,7 @@ void release_graph(bfs_graph* g) {
   if (!g) return;
   free_single_ws(g);
   free_multi_ws(g);
+  free_relabel(g);
   if (g->rp) cudaFree(g->rp);
   if (g->col) cudaFree(g->col);
   if (g->init_vis) cudaFree(g->init_vis);
@@ -252,9 +253,10 @@ static int check_params(const bfs_params& p) {
   if (p.blocks_per_sm < 0 || p.timeout_ms < 1 || p.test_barrier_extra < 0) return BFS_EINVAL;
   if (p.bu_chunk < 0 || p.bu_chunk > 65536) return BFS_EINVAL;
   if (p.bu_thread_max < 0 || p.bu_thread_max > (1 << 20)) return BFS_EINVAL;
-  if (p.ms_lanes < 1 || p.ms_lanes > 256 || p.ms_ring < 2 || p.ms_ring > 8 || p.ms_heavy_min < 0) return BFS_EINVAL;
+  if (p.ms_lanes < 1 || p.ms_lanes > 256 || p.ms_ring < 2 || p.ms_ring > 16 || p.ms_heavy_min < 0) return BFS_EINVAL;
   if (p.ms_degree_order < 0 || p.ms_degree_order > 1) return BFS_EINVAL;
   if (p.ms_alpha < 1) return BFS_EINVAL;
+  if (p.ms_relabel < 0 || p.ms_relabel > 1) return BFS_EINVAL;
   return BFS_OK;
 }
 
@@ -300,10 +302,11 @@ void bfs_params_default(bfs_params* p) {
   p->bu_chunk = 0;
   p->bu_thread_max = 32;
   p->ms_lanes = 256;
-  p->ms_ring = 8;
+  p->ms_ring = 16;
   p->ms_heavy_min = 256;
   p->ms_degree_order = 1;
   p->ms_alpha = 2;
+  p->ms_relabel = 1;
 }
 
 int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n, int64_t m,
@@ -339,7 +342,10 @@ int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_i
     if (e == cudaSuccess && m > 0) e = cudaMemcpy(g->col, col_idx, sizeof(int) * (size_t)m, kind);
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemcpy (graph)", __FILE__, __LINE__); break; }
     rc = row_ptr_bits == 32 ? validate_and_facts<int>(g, flags) : validate_and_facts<long long>(g, flags);
-    if (rc == BFS_OK && (flags & BFS_DEGREE_ORDER)) rc = reorder_by_degree(g);
+    if (rc == BFS_OK && (flags & BFS_DEGREE_ORDER)) {
+      rc = reorder_by_degree(g);
+      g->deg_ordered = rc == BFS_OK;
+    }
     if (rc == BFS_OK && !(flags & BFS_NO_HEAD)) rc = build_head(g);
   } while (0);
   if (rc != BFS_OK) {

@@ -134,6 +134,20 @@ struct SingleWs {
 
 namespace gbfs {
 struct MultiWs;
+
+// A copy of the graph with the vertices renumbered by decreasing degree (ties
+// by id): new id i is the i-th vertex of that order.  Multi-source levels run
+// on it, so the frontier masks of the high-degree vertices, which most
+// neighbour lists point to, share cache lines, and the degree-0 vertices
+// (ids >= n_live) are never scanned.  Lists are sorted by new id, i.e. highest
+// degree first.  Built once per graph, on first use.
+struct Relabel {
+  void* rp = nullptr;      // row pointers of the renumbered graph, same width as the graph's
+  int* col = nullptr;      // renumbered neighbour ids (m entries + 4 zero pads)
+  int* new_of = nullptr;   // [n] new id of every original vertex
+  int* old_of = nullptr;   // [n] original id of every new id
+  long long n_live = 0;    // vertices of degree > 0 (they take ids 0 .. n_live-1)
+};
 }
 
 struct bfs_graph {
@@ -150,6 +164,8 @@ struct bfs_graph {
   std::mutex mu;
   gbfs::SingleWs ws;
   gbfs::MultiWs* ms = nullptr;  // multi-source workspace (bfs_multi.cu)
+  gbfs::Relabel* rl = nullptr;  // degree-renumbered copy (bfs_reorder.cu), built on first use
+  bool deg_ordered = false;     // lists were sorted highest degree first at upload
 };
 
 namespace gbfs {
@@ -165,6 +181,8 @@ bool is_device_pointer(const void* p);
 int reorder_by_degree(bfs_graph* g);
 int build_head(bfs_graph* g);
 int vertices_by_degree(bfs_graph* g, int* order);
+int ensure_relabel(bfs_graph* g);  // builds g->rl once (caller holds g->mu)
+void free_relabel(bfs_graph* g);
 int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
@@ -176,7 +194,7 @@ int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, co
 // Serving groups (bfs_multi.cu): 64 lanes on one graph, lanes joining at level boundaries.
 struct ServeGroup;
 size_t serve_group_bytes(const bfs_graph* g, int ring);
-int serve_group_create(bfs_graph* g, int ring, int heavy_min, ServeGroup** out);
+int serve_group_create(bfs_graph* g, int ring, int heavy_min, int high_priority, ServeGroup** out);
 void serve_group_destroy(ServeGroup* G);
 cudaStream_t serve_group_stream(ServeGroup* G);
 unsigned long long serve_group_lanes(const ServeGroup* G);

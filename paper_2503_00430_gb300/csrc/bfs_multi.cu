@@ -71,7 +71,7 @@ struct MultiWs {
 
 namespace {
 
-constexpr int kMsMaxRing = 8;
+constexpr int kMsMaxRing = 16;
 #ifndef GBFS_MS_PULL_MINB
 #define GBFS_MS_PULL_MINB 3  // pull kernels: blocks of 256 per SM the register budget must allow
 #endif
@@ -137,6 +137,7 @@ struct MsArgs {
   const void* rp;
   const int* col;
   long long n;
+  long long n_live;            // pull, dense apply, compact: vertices [0, n_live) (the rest have degree 0)
   int nw;
   unsigned long long full[4];   // lanes of the group
   unsigned long long act[4];    // lanes present in the current frontier (the only ones that can advance)
@@ -402,13 +403,13 @@ __global__ void __launch_bounds__(256) k_ms_apply_dense(MsArgs A) {
   Mask<W> act_acc;
 #pragma unroll
   for (int k = 0; k < W; ++k) act_acc.w[k] = 0;
-  for (long long base = tid - (tid & 31); base < A.n; base += nth) {
+  for (long long base = tid - (tid & 31); base < A.n_live; base += nth) {
     const long long v = base + ms_lane();
     bool nz = false;
     Mask<W> nn;
 #pragma unroll
     for (int k = 0; k < W; ++k) nn.w[k] = 0;
-    if (v < A.n) {
+    if (v < A.n_live) {
       const Mask<W> a = load_mask<W>(A.acc + v * W);
       if (!is_zero<W>(a)) {
         Mask<W> x = load_mask<W>(A.X + v * W);
@@ -452,9 +453,9 @@ template <int W>
 __global__ void __launch_bounds__(256) k_ms_compact(MsArgs A) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
-  for (long long base = tid - (tid & 31); base < A.n; base += nth) {
+  for (long long base = tid - (tid & 31); base < A.n_live; base += nth) {
     const long long v = base + ms_lane();
-    const bool nz = v < A.n && !is_zero<W>(load_mask<W>(A.Fcur + v * W));
+    const bool nz = v < A.n_live && !is_zero<W>(load_mask<W>(A.Fcur + v * W));
     warp_append(nz, (int)v, &A.ctrl->nq, A.qnext);
   }
 }
@@ -468,15 +469,15 @@ __global__ void __launch_bounds__(256, GBFS_MS_PULL_MINB) k_ms_pull(MsArgs A) {
   Mask<W> act_acc;
 #pragma unroll
   for (int k = 0; k < W; ++k) act_acc.w[k] = 0;
-  for (long long base = tid - (tid & 31); base < A.n; base += nth) {
+  for (long long base = tid - (tid & 31); base < A.n_live; base += nth) {
     const long long oi = base + ms_lane();
-    const long long v = (A.order && oi < A.n) ? (long long)A.order[oi] : oi;
+    const long long v = (A.order && oi < A.n_live) ? (long long)A.order[oi] : oi;
     bool nz = false, defer = false;
     long long sv = 0, dv = 0;
     Mask<W> nn;
 #pragma unroll
     for (int k = 0; k < W; ++k) nn.w[k] = 0;
-    if (v < A.n) {
+    if (v < A.n_live) {
       Mask<W> x = load_mask<W>(A.X + v * W);
       if (!covers<W>(x, A.act)) {
         const long long s = rpv<RP>(A.rp, v), e = rpv<RP>(A.rp, v + 1);
@@ -728,28 +729,39 @@ __global__ void k_ms_zero(unsigned long long* p, long long count) {
 }
 
 // ---- writer: ring levels [l0, l0 + nlev) into dist[i][v] ----
-// A block owns a tile of 128 vertices.  Phase 1 (coalesced reads of the ring):
-// per (vertex, word) the lanes found in the window and the three bits of the
-// finding level's offset, bit-sliced over 64 lanes, go to shared memory.
-// Phase 2: each warp takes one word and a share of its 64 rows; each lane
-// loads the four planes of its four consecutive vertices once into registers
-// and, row by row, extracts its four entries, so the warp stores 128
-// consecutive entries of the row with one vector store per lane (4 bytes for
-// uint8, 16 for int32).  The first window writes every entry ("unreached"
-// where the lane was not found); later windows write only what they found and
-// skip rows with nothing found in the tile.
+// A block owns a tile of 128 vertices (caller's ids).
+// Phase 1, one thread per (vertex, word): the vertex's masks of the window's
+// levels (coalesced reads; on a renumbered graph at its new id, and a vertex
+// of degree 0 is reached only by the lanes it is the source of - level 0,
+// first window - which X holds) become, per lane, the offset of the level
+// that found it, bit-sliced over the 64 lanes of the word (four planes) plus
+// the found mask.  Every group of four lanes (a nibble of each plane) then
+// becomes one 32-bit word of four output bytes: spread4 moves bit i of a
+// nibble to byte i, so byte i = found ? base + offset : 255, four lanes at a
+// time without branches (base = l0 for uint8 rows, 0 for int32 rows, which add
+// l0 when they widen).  The words go to shared memory as [word][nibble][vertex]
+// (vertex index XOR-swizzled by the word, so the four threads of a vertex hit
+// different banks).
+// Phase 2, one thread per (word, nibble, four consecutive vertices): one
+// 16-byte shared load, a 4x4 byte transpose (__byte_perm) gives the four rows'
+// entries of those vertices, so a warp stores 128 consecutive entries of a row
+// per instruction (4 bytes a lane for uint8, 16 for int32).  The first window
+// writes every entry; later windows write only what they found and skip rows
+// with nothing found in the tile.
 constexpr int kWt = 128;
 
+// Bit i of a nibble (x < 16) to bit 0 of byte i: the four shifted copies of x
+// (by 0, 7, 14 and 21 bits) do not overlap, so the product has no carries.
+__device__ __forceinline__ unsigned spread4(unsigned x) { return (x * 0x00204081u) & 0x01010101u; }
+
 template <int W, typename T>
-__global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, long long n, int ring, int l0,
-                                                  int nlev, int lanes, bool first, T* dist, T unreached) {
-  __shared__ unsigned long long pl[4][W][kWt];
+__global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, const unsigned long long* X,
+                                                  const int* new_of, long long n, long long n_live, int ring, int l0,
+                                                  int nlev, int lanes, bool first, T* dist) {
+  __shared__ __align__(16) unsigned code[W][16][kWt];
   __shared__ unsigned long long tile_or[W];
   const long long ntiles = (n + kWt - 1) / kWt;
-  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int wpw = (int)nwarp / W;                 // warps per word
-  const int w = (int)warp % W, part = (int)warp / W;
-  const int rows_per = (64 + wpw - 1) / wpw;
+  const unsigned base = sizeof(T) == 1 ? (unsigned)l0 : 0u;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long v0 = tile * kWt;
     if (threadIdx.x < W) tile_or[threadIdx.x] = 0ull;
@@ -757,69 +769,91 @@ __global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, l
     for (int idx = threadIdx.x; idx < kWt * W; idx += blockDim.x) {
       const int j = idx / W, ww = idx % W;
       const long long v = v0 + j;
-      unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0;
+      unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0, p3 = 0;
       if (v < n) {
-        unsigned long long m[kMsMaxRing];
+        const long long vv = new_of ? (long long)new_of[v] : v;
+        if (vv < n_live) {
+          unsigned long long m[kMsMaxRing];
 #pragma unroll
-        for (int l = 0; l < kMsMaxRing; ++l)
-          m[l] = l < nlev ? F[(long long)((l0 + l) % ring) * n * W + v * W + ww] : 0ull;
+          for (int l = 0; l < kMsMaxRing; ++l)
+            m[l] = l < nlev ? F[(long long)((l0 + l) % ring) * n * W + vv * W + ww] : 0ull;
 #pragma unroll
-        for (int l = kMsMaxRing - 1; l >= 0; --l) {
-          f |= m[l];
-          p0 = (p0 & ~m[l]) | ((l & 1) ? m[l] : 0ull);
-          p1 = (p1 & ~m[l]) | ((l & 2) ? m[l] : 0ull);
-          p2 = (p2 & ~m[l]) | ((l & 4) ? m[l] : 0ull);
+          for (int l = kMsMaxRing - 1; l >= 0; --l) {
+            f |= m[l];
+            p0 = (p0 & ~m[l]) | ((l & 1) ? m[l] : 0ull);
+            p1 = (p1 & ~m[l]) | ((l & 2) ? m[l] : 0ull);
+            p2 = (p2 & ~m[l]) | ((l & 4) ? m[l] : 0ull);
+            p3 = (p3 & ~m[l]) | ((l & 8) ? m[l] : 0ull);
+          }
+        } else if (first) {
+          f = X[vv * W + ww];
         }
       }
-      pl[0][ww][j] = f;
-      pl[1][ww][j] = p0;
-      pl[2][ww][j] = p1;
-      pl[3][ww][j] = p2;
       if (!first && f) atomicOr(&tile_or[ww], f);
+      const int js = j ^ (8 * ww);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const unsigned sf = spread4((unsigned)(f >> (4 * k)) & 0xfu);
+        const unsigned lv = spread4((unsigned)(p0 >> (4 * k)) & 0xfu) + 2u * spread4((unsigned)(p1 >> (4 * k)) & 0xfu) +
+                            4u * spread4((unsigned)(p2 >> (4 * k)) & 0xfu) + 8u * spread4((unsigned)(p3 >> (4 * k)) & 0xfu);
+        code[ww][k][js] = lv + base * sf + (sf ^ 0x01010101u) * 255u;
+      }
     }
     __syncthreads();
-    if ((int)warp < wpw * W) {
-      const int j0 = 4 * (int)lane;
-      unsigned long long f[4], q0[4], q1[4], q2[4];
+    const bool full_tile = v0 + kWt <= n;
+    for (int task = threadIdx.x; task < W * 16 * (kWt / 4); task += blockDim.x) {
+      const int q = task % (kWt / 4), k = (task / (kWt / 4)) % 16, ww = task / (16 * (kWt / 4));
+      const int r0 = 64 * ww + 4 * k;
+      if (r0 >= lanes) continue;
+      const uint4 c = *reinterpret_cast<const uint4*>(&code[ww][k][(4 * q) ^ (8 * ww)]);
+      // c.x..c.w: vertices 4q..4q+3, byte i = row r0 + i.  Transpose to rows.
+      const unsigned a = __byte_perm(c.x, c.y, 0x5140), b = __byte_perm(c.z, c.w, 0x5140);
+      const unsigned d = __byte_perm(c.x, c.y, 0x7362), e = __byte_perm(c.z, c.w, 0x7362);
+      const unsigned rowv[4] = {__byte_perm(a, b, 0x5410), __byte_perm(a, b, 0x7632), __byte_perm(d, e, 0x5410),
+                                __byte_perm(d, e, 0x7632)};
+      const long long va = v0 + 4 * q;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        f[t] = pl[0][w][j0 + t];
-        q0[t] = pl[1][w][j0 + t];
-        q1[t] = pl[2][w][j0 + t];
-        q2[t] = pl[3][w][j0 + t];
-      }
-      const long long va = v0 + j0;
-      const bool full_tile = v0 + kWt <= n;
-      const int b0 = part * rows_per, b1 = min(64, b0 + rows_per);
-      for (int b = b0; b < b1; ++b) {
-        const int i = 64 * w + b;
-        if (i >= lanes) break;
-        if (!first && !((tile_or[w] >> b) & 1ull)) continue;
-        T* row = dist + (long long)i * n + va;
-        T val[4];
-        bool fnd[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          fnd[t] = (f[t] >> b) & 1ull;
-          const int lv = (int)(((q0[t] >> b) & 1ull) | (((q1[t] >> b) & 1ull) << 1) | (((q2[t] >> b) & 1ull) << 2));
-          val[t] = fnd[t] ? (T)(l0 + lv) : unreached;
-        }
-        if (first && full_tile && (reinterpret_cast<uintptr_t>(row) % (4 * sizeof(T))) == 0) {
-          if constexpr (sizeof(T) == 1) {
-            *reinterpret_cast<uchar4*>(row) = make_uchar4((unsigned char)val[0], (unsigned char)val[1],
-                                                          (unsigned char)val[2], (unsigned char)val[3]);
+      for (int i = 0; i < 4; ++i) {
+        const int r = r0 + i;
+        if (r >= lanes) break;
+        if (!first && !((tile_or[ww] >> (4 * k + i)) & 1ull)) continue;
+        const unsigned w4 = rowv[i];
+        if (!first && w4 == 0xffffffffu) continue;
+        T* row = dist + (long long)r * n + va;
+        if constexpr (sizeof(T) == 1) {
+          if (first && full_tile && (reinterpret_cast<uintptr_t>(row) & 3u) == 0) {
+            *reinterpret_cast<unsigned*>(row) = w4;
           } else {
-            *reinterpret_cast<int4*>(row) = make_int4((int)val[0], (int)val[1], (int)val[2], (int)val[3]);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const unsigned by = (w4 >> (8 * t)) & 0xffu;
+              if (va + t < n && (first || by != 0xffu)) row[t] = (T)by;
+            }
           }
         } else {
+          int x[4];
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            if (va + t < n && (first || fnd[t])) row[t] = val[t];
+          for (int t = 0; t < 4; ++t) {
+            const unsigned by = (w4 >> (8 * t)) & 0xffu;
+            x[t] = by == 0xffu ? -1 : l0 + (int)by;
+          }
+          if (first && full_tile && (reinterpret_cast<uintptr_t>(row) & 15u) == 0) {
+            *reinterpret_cast<int4*>(row) = make_int4(x[0], x[1], x[2], x[3]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (va + t < n && (first || x[t] >= 0)) row[t] = (T)x[t];
+          }
         }
       }
     }
     __syncthreads();
   }
+}
+
+// Caller's vertex ids -> renumbered ids, in place.
+__global__ void k_ms_map(int* ids, int count, const int* new_of) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) ids[i] = new_of[ids[i]];
 }
 
 template <typename RP>
@@ -890,17 +924,24 @@ namespace {
 // kernel needs is read from the control block on the device.
 // A push level whose frontier's degree sum exceeds n / 8 touches a large share
 // of the vertices: it keeps no touched list and applies by a scan of all vertices.
+// A push level's kernels get grids sized to the frontier: nf vertices whose
+// degrees sum to mf (an upper bound is enough) need nf planning threads, at
+// most nf + mf / kMsPushChunk pushing warps and mf applying threads.
 template <int W, typename RP>
-void ms_step(MsArgs A, bool push, bool dense, long long nf, unsigned long long* Fn, long long n, int grid,
-             cudaStream_t s) {
+void ms_step(MsArgs A, bool push, bool dense, long long nf, long long mf, unsigned long long* Fn, long long n,
+             int grid, cudaStream_t s) {
   cudaMemsetAsync(A.ctrl, 0, sizeof(MsCtrl), s);
   A.dense = push && dense ? 1 : 0;
   if (push) {
+    auto fit = [grid](long long units, long long per_block) {
+      const long long b = (units + per_block - 1) / per_block;
+      return (int)(b < 1 ? 1 : (b > grid ? grid : b));
+    };
     k_ms_zero<<<grid, 256, 0, s>>>(Fn, n * W);
-    k_ms_push_plan<RP><<<grid, 256, 0, s>>>(A, nf);
-    k_ms_push<W, RP><<<grid, 256, 0, s>>>(A, nf);
+    k_ms_push_plan<RP><<<fit(nf, 256), 256, 0, s>>>(A, nf);
+    k_ms_push<W, RP><<<fit(nf + mf / kMsPushChunk + 1, 8), 256, 0, s>>>(A, nf);
     if (A.dense) k_ms_apply_dense<W, RP><<<grid, 256, 0, s>>>(A);
-    else k_ms_apply<W, RP><<<grid, 256, 0, s>>>(A);
+    else k_ms_apply<W, RP><<<fit(mf, 256), 256, 0, s>>>(A);
   } else {
     k_ms_pull<W, RP><<<grid, 256, 0, s>>>(A);
     k_ms_heavy_chunks<W, RP><<<grid, 256, 0, s>>>(A);
@@ -914,10 +955,12 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   MultiWs& ws = *g->ms;
   const long long n = g->n;
   const int grid = g->num_sms * 8, block = 256;
+  const Relabel* rl = p.ms_relabel ? g->rl : nullptr;
   MsArgs A{};
-  A.rp = g->rp;
-  A.col = g->col;
+  A.rp = rl ? rl->rp : g->rp;
+  A.col = rl ? rl->col : g->col;
   A.n = n;
+  A.n_live = rl ? rl->n_live : n;
   A.nw = g->nw;
   for (int k = 0; k < 4; ++k) {
     const int lo = 64 * k;
@@ -931,7 +974,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   A.heavy = ws.heavy;
   A.ctrl = ws.ctrl;
   A.heavy_min = p.ms_heavy_min;
-  A.order = p.ms_degree_order ? ws.order : nullptr;
+  A.order = (!rl && p.ms_degree_order) ? ws.order : nullptr;
   A.want_queue = 0;
   const int K = ws.ring;
   auto slot = [&](int l) { return ws.F + (long long)(l % K) * n * W; };
@@ -941,12 +984,16 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
   GBFS_CUDA(cudaMemcpyAsync(ws.d_src, srcs, sizeof(int) * (size_t)lanes, cudaMemcpyHostToDevice, s));
   GBFS_CUDA(cudaMemcpyAsync(ws.q[0], uniq.data(), sizeof(int) * uniq.size(), cudaMemcpyHostToDevice, s));
+  if (rl) {
+    k_ms_map<<<1, 256, 0, s>>>(ws.d_src, lanes, rl->new_of);
+    k_ms_map<<<1, 256, 0, s>>>(ws.q[0], (int)uniq.size(), rl->new_of);
+  }
   k_ms_zero<<<grid, block, 0, s>>>(ws.X, n * W);
   k_ms_zero<<<grid, block, 0, s>>>(slot(0), n * W);
   A.Fcur = slot(0);
   k_ms_seed<W><<<1, 256, 0, s>>>(A, ws.d_src, lanes);
   GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(MsCtrl), s));
-  k_ms_degree_sum<RP><<<1, 256, 0, s>>>(reinterpret_cast<const RP*>(g->rp), ws.q[0], (int)uniq.size(), &ws.ctrl->mf);
+  k_ms_degree_sum<RP><<<1, 256, 0, s>>>(reinterpret_cast<const RP*>(A.rp), ws.q[0], (int)uniq.size(), &ws.ctrl->mf);
   GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
   GBFS_CUDA(cudaStreamSynchronize(s));
   long long nf = (long long)uniq.size(), mf = (long long)ws.h_ctrl->mf, nf_prev = nf;
@@ -959,7 +1006,8 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
   auto flush = [&](int upto) -> int {  // write levels [flushed, upto]
     const int nlev = upto - flushed + 1;
     if (nlev <= 0) return BFS_OK;
-    k_ms_write<W, T><<<g->num_sms * 16, 256, 0, s>>>(ws.F, n, K, flushed, nlev, lanes, first_flush, dist, unreached);
+    k_ms_write<W, T><<<g->num_sms * 16, 256, 0, s>>>(ws.F, ws.X, rl ? rl->new_of : nullptr, n, A.n_live, K, flushed,
+                                                     nlev, lanes, first_flush, dist);
     GBFS_CUDA(cudaGetLastError());
     first_flush = false;
     flushed = upto + 1;
@@ -989,7 +1037,7 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
     A.qcur = ws.q[qc];
     A.qnext = ws.q[qc ^ 1];
     const bool dense = mf > n / 8;
-    ms_step<W, RP>(A, push, dense, nf, Fn, n, grid, s);
+    ms_step<W, RP>(A, push, dense, nf, mf, Fn, A.n_live, grid, s);
     queue_ready = push && !dense;
     GBFS_CUDA(cudaGetLastError());
     GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, s));
@@ -1043,6 +1091,10 @@ int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, co
   if (ring > kMsMaxRing) ring = kMsMaxRing;
   int rc = ensure_multi_ws(g, ring);
   if (rc != BFS_OK) return rc;
+  if (p.ms_relabel) {
+    rc = ensure_relabel(g);
+    if (rc != BFS_OK) return rc;
+  }
   MultiWs& ws = *g->ms;
   GBFS_CUDA(cudaStreamWaitEvent(s, ws.done, 0));
   const bool host_out = !is_device_pointer(dist);
@@ -1115,6 +1167,7 @@ struct ServeGroup {
   cudaEvent_t ev_level = nullptr;
   int L = 0, qc = 0, flushed = 0;
   long long nf = 0;
+  long long mf = 0;        // degree sum of the current frontier (an upper bound after joins)
   unsigned long long lanes = 0, act = 0, first = 0;
   bool launched = false;
 };
@@ -1145,7 +1198,7 @@ __global__ void k_serve_seed(unsigned long long* X, unsigned long long* Fcur, in
 __global__ void __launch_bounds__(256) k_serve_write(const unsigned long long* F, long long n, int ring, int l0,
                                                      int nlev, const unsigned long long* valid, unsigned long long lanes,
                                                      unsigned long long first, int* const* out, const int* join) {
-  __shared__ unsigned long long pl[4][kWt];
+  __shared__ unsigned long long pl[5][kWt];
   __shared__ unsigned long long vmask[kMsMaxRing];
   if (threadIdx.x < kMsMaxRing) vmask[threadIdx.x] = threadIdx.x < (unsigned)nlev ? valid[threadIdx.x] : 0ull;
   const long long ntiles = (n + kWt - 1) / kWt;
@@ -1155,7 +1208,7 @@ __global__ void __launch_bounds__(256) k_serve_write(const unsigned long long* F
     const long long v0 = tile * kWt;
     for (int j = threadIdx.x; j < kWt; j += blockDim.x) {
       const long long v = v0 + j;
-      unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0;
+      unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0, p3 = 0;
       if (v < n) {
         for (int l = nlev - 1; l >= 0; --l) {
           const unsigned long long m = F[(long long)((l0 + l) % ring) * n + v] & vmask[l];
@@ -1163,12 +1216,14 @@ __global__ void __launch_bounds__(256) k_serve_write(const unsigned long long* F
           p0 = (p0 & ~m) | ((l & 1) ? m : 0ull);
           p1 = (p1 & ~m) | ((l & 2) ? m : 0ull);
           p2 = (p2 & ~m) | ((l & 4) ? m : 0ull);
+          p3 = (p3 & ~m) | ((l & 8) ? m : 0ull);
         }
       }
       pl[0][j] = f;
       pl[1][j] = p0;
       pl[2][j] = p1;
       pl[3][j] = p2;
+      pl[4][j] = p3;
     }
     __syncthreads();
     unsigned long long todo = lanes;
@@ -1185,7 +1240,7 @@ __global__ void __launch_bounds__(256) k_serve_write(const unsigned long long* F
         if (v0 + j >= n) break;
         if ((pl[0][j] >> i) & 1ull) {
           const int lv = (int)(((pl[1][j] >> i) & 1ull) | (((pl[2][j] >> i) & 1ull) << 1) |
-                               (((pl[3][j] >> i) & 1ull) << 2));
+                               (((pl[3][j] >> i) & 1ull) << 2) | (((pl[4][j] >> i) & 1ull) << 3));
           row[j] = l0 + lv - jn;
         } else if (fst) {
           row[j] = -1;
@@ -1202,6 +1257,7 @@ void serve_step(ServeGroup* G, bool push) {
   A.rp = G->g->rp;
   A.col = G->g->col;
   A.n = G->n;
+  A.n_live = G->n;
   A.nw = G->g->nw;
   A.full[0] = G->lanes;
   A.act[0] = G->act;
@@ -1219,7 +1275,7 @@ void serve_step(ServeGroup* G, bool push) {
   A.ctrl = G->ctrl;
   A.heavy_min = G->heavy_min;
   A.want_queue = 1;
-  ms_step<1, RP>(A, push, false, G->nf, A.Fnext, G->n, G->g->num_sms * 8, G->stream);
+  ms_step<1, RP>(A, push, false, G->nf, G->mf, A.Fnext, G->n, G->g->num_sms * 8, G->stream);
 }
 
 int serve_flush(ServeGroup* G, int upto) {
@@ -1250,7 +1306,7 @@ size_t serve_group_bytes(const bfs_graph* g, int ring) {
   return n * 8 * (2 + (size_t)ring) + n * 4 * 4 + heavy + (size_t)g->nw * 4 + 4096;
 }
 
-int serve_group_create(bfs_graph* g, int ring, int heavy_min, ServeGroup** out) {
+int serve_group_create(bfs_graph* g, int ring, int heavy_min, int high_priority, ServeGroup** out) {
   ServeGroup* G = new ServeGroup();
   G->g = g;
   G->ring = ring < 2 ? 2 : (ring > kMsMaxRing ? kMsMaxRing : ring);
@@ -1271,7 +1327,8 @@ int serve_group_create(bfs_graph* g, int ring, int heavy_min, ServeGroup** out) 
     const size_t heavy_cap = std::min(n, (size_t)g->m / (size_t)(G->heavy_min + 1)) + 2;
     if (e == cudaSuccess) e = cudaMalloc(&G->heavy, sizeof(MsHeavy) * heavy_cap);
     if (e == cudaSuccess) e = cudaMalloc(&G->order, 4 * n);
-    if (e == cudaSuccess) e = cudaMalloc(&G->ctrl, sizeof(MsCtrl) * 2);
+    // The control block, then the per-level lane masks of a flush (serve_flush).
+    if (e == cudaSuccess) e = cudaMalloc(&G->ctrl, sizeof(MsCtrl) + sizeof(unsigned long long) * kMsMaxRing);
     if (e == cudaSuccess) e = cudaMallocHost(&G->h_ctrl, sizeof(MsCtrl));
     if (e == cudaSuccess) e = cudaMalloc(&G->d_out, sizeof(int*) * 64);
     if (e == cudaSuccess) e = cudaMalloc(&G->d_join, sizeof(int) * 64);
@@ -1281,7 +1338,10 @@ int serve_group_create(bfs_graph* g, int ring, int heavy_min, ServeGroup** out) 
     if (e == cudaSuccess) e = cudaMallocHost(&G->h_join, sizeof(int) * 64);
     if (e == cudaSuccess) e = cudaMallocHost(&G->h_new, sizeof(int) * 64);
     if (e == cudaSuccess) e = cudaMallocHost(&G->h_newlane, sizeof(int) * 64);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G->stream, cudaStreamNonBlocking);
+    int prio_lo = 0, prio_hi = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&G->stream, cudaStreamNonBlocking, high_priority ? prio_hi : prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->ev_level, cudaEventDisableTiming);
     if (e != cudaSuccess) { rc = cuda_fail(e, "serving group allocation", __FILE__, __LINE__); break; }
     rc = vertices_by_degree(g, G->order);
@@ -1336,6 +1396,7 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
     G->qc = 0;
     G->flushed = 0;
     G->nf = 0;
+    G->mf = 0;
     G->act = 0;
     k_ms_zero<<<grid, 256, 0, G->stream>>>(G->X, G->n);
     k_ms_zero<<<grid, 256, 0, G->stream>>>(G->F, G->n);
@@ -1359,6 +1420,7 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
                                         G->d_newlane, count);
   GBFS_CUDA(cudaGetLastError());
   G->nf += count;
+  G->mf += (long long)count * G->g->max_deg;  // the sources' degrees are not known on the host
   G->lanes |= mask;
   G->act |= mask;
   G->first |= mask;
@@ -1397,6 +1459,7 @@ int serve_group_finish(ServeGroup* G, unsigned long long* retired) {
   const unsigned long long act_next = c.act[0] & G->lanes;
   const unsigned long long done = G->lanes & ~act_next;
   G->nf = (long long)c.nf;
+  G->mf = (long long)c.mf;
   G->act = act_next;
   if (done) {
     // The finished lanes' last frontier is level L (their level L+1 is empty);

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 #include <cub/device/device_segmented_sort.cuh>
 
 #include "bfs_internal.cuh"
@@ -117,6 +118,123 @@ int degree_order_impl(bfs_graph* g, int* order) {
 // similar length.
 int vertices_by_degree(bfs_graph* g, int* order) {
   return g->rp_bits == 32 ? degree_order_impl<int>(g, order) : degree_order_impl<long long>(g, order);
+}
+
+namespace {
+
+// new_of[old_of[i]] = i and the degree of new vertex i (deg[n] = 0, so an
+// exclusive scan over n + 1 entries gives the renumbered row pointers).
+template <typename RP>
+__global__ void k_inverse_degrees(const RP* rp, const int* old_of, long long n, int* new_of, RP* deg) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i <= n; i += nth) {
+    if (i == n) {
+      deg[n] = 0;
+      continue;
+    }
+    const int o = old_of[i];
+    new_of[o] = (int)i;
+    deg[i] = rp[(long long)o + 1] - rp[o];
+  }
+}
+
+// Warp per new vertex: its list, neighbour ids renumbered.
+template <typename RP>
+__global__ void k_relabel_lists(const RP* rp, const int* col, const RP* rp2, const int* old_of, const int* new_of,
+                                long long n, int* col2) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const unsigned lane = threadIdx.x & 31u;
+  for (long long i = gw; i < n; i += nwarps) {
+    const int o = old_of[i];
+    const long long s = (long long)rp[o], d = (long long)rp[(long long)o + 1] - s, s2 = (long long)rp2[i];
+    for (long long j = lane; j < d; j += 32) col2[s2 + j] = new_of[col[s + j]];
+  }
+}
+
+template <typename RP>
+int relabel_impl(bfs_graph* g, Relabel* r) {
+  const long long n = g->n, m = g->m;
+  const size_t mpad = (size_t)((m + 3) / 4 * 4 + 4);
+  RP* rp2 = nullptr;
+  RP* deg = nullptr;
+  int* tmp_col = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  int rc = BFS_OK;
+  do {
+    cudaError_t e = cudaMalloc(&r->old_of, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&r->new_of, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&rp2, sizeof(RP) * (size_t)(n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&deg, sizeof(RP) * (size_t)(n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&r->col, sizeof(int) * mpad);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc (relabel)", __FILE__, __LINE__); break; }
+    r->rp = rp2;
+    rc = degree_order_impl<RP>(g, r->old_of);
+    if (rc != BFS_OK) break;
+    const int grid = g->num_sms * 8, block = 256;
+    k_inverse_degrees<RP><<<grid, block>>>(reinterpret_cast<const RP*>(g->rp), r->old_of, n, r->new_of, deg);
+    e = cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, deg, rp2, n + 1);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes);
+    if (e == cudaSuccess) e = cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, deg, rp2, n + 1);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "relabel scan", __FILE__, __LINE__); break; }
+    cudaFree(tmp);
+    tmp = nullptr;
+    e = cudaMemset(r->col + m, 0, sizeof(int) * (mpad - (size_t)m));
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemset (relabel)", __FILE__, __LINE__); break; }
+    // Degree-ordered lists map to ascending new ids; other lists are sorted
+    // after renumbering (the segmented sort takes 32-bit counts).
+    const bool sort = !g->deg_ordered && m > 0 && m < (1ll << 31);
+    if (sort) {
+      e = cudaMalloc(&tmp_col, sizeof(int) * (size_t)m);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMalloc (relabel sort)", __FILE__, __LINE__); break; }
+    }
+    k_relabel_lists<RP><<<grid, block>>>(reinterpret_cast<const RP*>(g->rp), g->col, rp2, r->old_of, r->new_of, n,
+                                         sort ? tmp_col : r->col);
+    if (sort) {
+      e = cub::DeviceSegmentedSort::SortKeys(nullptr, tmp_bytes, tmp_col, r->col, (int)m, (int)n, rp2, rp2 + 1);
+      if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes);
+      if (e == cudaSuccess)
+        e = cub::DeviceSegmentedSort::SortKeys(tmp, tmp_bytes, tmp_col, r->col, (int)m, (int)n, rp2, rp2 + 1);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "relabel sort", __FILE__, __LINE__); break; }
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { rc = cuda_fail(e, "relabel", __FILE__, __LINE__); break; }
+    r->n_live = n - g->isolated;
+  } while (0);
+  cudaFree(deg);
+  cudaFree(tmp_col);
+  cudaFree(tmp);
+  return rc;
+}
+
+}  // namespace
+
+int ensure_relabel(bfs_graph* g) {
+  if (g->rl) return BFS_OK;
+  Relabel* r = new Relabel();
+  const int rc = g->rp_bits == 32 ? relabel_impl<int>(g, r) : relabel_impl<long long>(g, r);
+  if (rc != BFS_OK) {
+    cudaFree(r->rp);
+    cudaFree(r->col);
+    cudaFree(r->new_of);
+    cudaFree(r->old_of);
+    delete r;
+    return rc;
+  }
+  g->rl = r;
+  return BFS_OK;
+}
+
+void free_relabel(bfs_graph* g) {
+  if (!g->rl) return;
+  cudaFree(g->rl->rp);
+  cudaFree(g->rl->col);
+  cudaFree(g->rl->new_of);
+  cudaFree(g->rl->old_of);
+  delete g->rl;
+  g->rl = nullptr;
 }
 
 int reorder_by_degree(bfs_graph* g) {

@@ -1,16 +1,19 @@
 // Serving loop: resident graphs, a stream of (graph, source) queries, and
 // continuous batching into 64-lane multi-source groups.
 //
-// A server thread owns one lane group per graph (created on first use if the
-// device-memory budget allows).  Each pass it (1) moves submitted queries to
-// their graph's queue, (2) admits queued queries into free lanes - a query
-// needs a free lane and, if its output is host memory, a device staging
-// buffer of 4n bytes within the budget - where they join the running group at
-// its next level, (3) launches one level of every busy group (each on its own
-// stream, so groups on different graphs overlap on the GPU); each group moves
-// on to its next level as soon as its own level has finished (groups are not
-// in lockstep), retiring lanes whose frontier emptied: their rows are written
-// and, for host outputs, copied back; a query is done when its copy is.
+// Every registered graph has one lane group (created on its first query if
+// the device-memory budget allows) and one worker thread that drives it, so
+// groups on different graphs advance independently, each on its own stream.
+// A worker loops: (1) waits for its group's launched level and retires lanes
+// whose frontier emptied (their rows are written and, for host outputs,
+// copied back; a query is done when its copy is); (2) admits queued queries
+// into free lanes - a query needs a free lane and, if its output is host
+// memory, a device staging buffer of 4n bytes within the budget - where they
+// join the running group at its next level; (3) launches the next level.
+// Large-diameter graphs (average degree below the paper's threshold of
+// Section 3) run thousands of short levels: their group's stream gets the
+// highest priority, so its small kernels are scheduled ahead of the dense
+// levels of other groups instead of queueing behind them.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -52,29 +55,33 @@ struct Query {
 struct GraphEntry {
   bfs_graph* g = nullptr;
   gbfs::ServeGroup* grp = nullptr;
-  std::deque<Query*> pending;
+  std::deque<Query*> pending;         // submitted, not yet taken by the worker (guarded by the server mutex)
+  std::condition_variable cv;         // wakes the worker (with the server mutex)
+  // Owned by the worker thread:
+  std::deque<Query*> waiting;         // taken, waiting for a lane or memory
   Query* lane_q[64] = {};
   std::vector<int32_t*> staging_free;
+  std::vector<int32_t*> staging_all;
+  std::vector<Query*> completing;
+  std::thread th;
 };
 
 }  // namespace
 
 struct bfs_server {
   size_t budget = 0;
-  size_t used = 0;
+  size_t used = 0;                    // guarded by mu
   bfs_params p{};
   int device = 0;
-  std::vector<GraphEntry*> graphs;  // entries never move once added
+  std::vector<GraphEntry*> graphs;    // entries never move once added (guarded by mu)
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<Query*> inbox;
-  size_t inbox_cap = (size_t)1 << 20;
+  std::condition_variable cv_done;
+  size_t queued = 0;                  // submitted, not yet admitted
+  size_t queue_cap = (size_t)1 << 20;
   std::unordered_map<uint64_t, Query*> tickets;
-  std::vector<Query*> completing;
   uint64_t next_ticket = 1;
   bool stop = false;
   std::atomic<int> error{BFS_OK};
-  std::thread th;
 };
 
 namespace {
@@ -91,116 +98,40 @@ void fill_stats(const Query* q, bfs_query_stats* st) {
   st->status = q->status;
 }
 
-// One pass of the server; returns true if any work is in flight or queued.
-bool server_pass(bfs_server* S) {
-  std::vector<GraphEntry*> ges;
-  bool admit = true;
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    while (!S->inbox.empty()) {
-      Query* q = S->inbox.front();
-      S->inbox.pop_front();
-      S->graphs[q->graph]->pending.push_back(q);
-    }
-    ges = S->graphs;
-    admit = !S->stop;
+// Takes `bytes` of the budget; false if they do not fit.
+bool reserve(bfs_server* S, size_t bytes) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->used + bytes > S->budget) return false;
+  S->used += bytes;
+  return true;
+}
+
+// The group's launched level is done: retire lanes whose frontier emptied.
+void finish_level(bfs_server* S, GraphEntry* ge) {
+  unsigned long long retired = 0;
+  const int rc = gbfs::serve_group_finish(ge->grp, &retired);
+  if (rc != BFS_OK) S->error = rc;
+  while (retired) {
+    const int i = __builtin_ctzll(retired);
+    retired &= retired - 1;
+    Query* q = ge->lane_q[i];
+    ge->lane_q[i] = nullptr;
+    if (!q) continue;
+    q->levels = gbfs::serve_group_level(ge->grp) - q->join;
+    cudaStream_t st = gbfs::serve_group_stream(ge->grp);
+    if (q->host_out)
+      cudaMemcpyAsync(q->user_out, q->dev_out, sizeof(int32_t) * (size_t)ge->g->n, cudaMemcpyDeviceToHost, st);
+    cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
+    cudaEventRecord(q->ev, st);
+    ge->completing.push_back(q);
   }
-  bool busy = false;
-  for (GraphEntry* ge : ges) {
-    // A group advances as soon as its own level is done, independently of the others.
-    if (ge->grp) {
-      const int r = gbfs::serve_group_ready(ge->grp);
-      if (r == 0) {
-        busy = true;
-        continue;
-      }
-      if (r == 1) {
-        unsigned long long retired = 0;
-        const int rc = gbfs::serve_group_finish(ge->grp, &retired);
-        if (rc != BFS_OK) S->error = rc;
-        while (retired) {
-          const int i = __builtin_ctzll(retired);
-          retired &= retired - 1;
-          Query* q = ge->lane_q[i];
-          ge->lane_q[i] = nullptr;
-          if (!q) continue;
-          q->levels = gbfs::serve_group_level(ge->grp) - q->join;
-          cudaStream_t st = gbfs::serve_group_stream(ge->grp);
-          if (q->host_out)
-            cudaMemcpyAsync(q->user_out, q->dev_out, sizeof(int32_t) * (size_t)ge->g->n, cudaMemcpyDeviceToHost, st);
-          cudaEventCreateWithFlags(&q->ev, cudaEventDisableTiming);
-          cudaEventRecord(q->ev, st);
-          S->completing.push_back(q);
-        }
-      }
-    }
-    // Admission into free lanes, then the next level.
-    const unsigned long long in_use = ge->grp ? gbfs::serve_group_lanes(ge->grp) : 0ull;
-    std::vector<int> lanes, srcs;
-    std::vector<int*> outs;
-    while (admit && !ge->pending.empty()) {
-      int lane = -1;
-      for (int i = 0; i < 64; ++i)
-        if (!((in_use >> i) & 1ull) && ge->lane_q[i] == nullptr) {
-          bool taken = false;
-          for (int l : lanes) taken |= (l == i);
-          if (!taken) {
-            lane = i;
-            break;
-          }
-        }
-      if (lane < 0) break;
-      Query* q = ge->pending.front();
-      const size_t nbytes = sizeof(int32_t) * (size_t)ge->g->n;
-      if (!ge->grp) {
-        const size_t need = gbfs::serve_group_bytes(ge->g, S->p.ms_ring);
-        if (S->used + need > S->budget) break;
-        int rc = gbfs::serve_group_create(ge->g, S->p.ms_ring, S->p.ms_heavy_min, &ge->grp);
-        if (rc != BFS_OK) {
-          S->error = rc;
-          break;
-        }
-        S->used += need;
-      }
-      if (q->host_out) {
-        if (ge->staging_free.empty()) {
-          if (S->used + nbytes > S->budget) break;
-          int32_t* buf = nullptr;
-          if (cudaMalloc(&buf, nbytes) != cudaSuccess) {
-            cudaGetLastError();
-            break;
-          }
-          S->used += nbytes;
-          ge->staging_free.push_back(buf);
-        }
-        q->dev_out = ge->staging_free.back();
-        ge->staging_free.pop_back();
-      } else {
-        q->dev_out = q->user_out;
-      }
-      ge->pending.pop_front();
-      q->lane = lane;
-      q->t_start = now_ns();
-      q->join = gbfs::serve_group_lanes(ge->grp) ? gbfs::serve_group_level(ge->grp) : 0;
-      ge->lane_q[lane] = q;
-      lanes.push_back(lane);
-      srcs.push_back(q->src);
-      outs.push_back(q->dev_out);
-    }
-    if (!lanes.empty()) {
-      const int rc = gbfs::serve_group_join(ge->grp, (int)lanes.size(), lanes.data(), srcs.data(), outs.data());
-      if (rc != BFS_OK) S->error = rc;
-    }
-    if (ge->grp && gbfs::serve_group_lanes(ge->grp)) {
-      const int rc = gbfs::serve_group_launch(ge->grp, S->p.tau_inv);
-      if (rc != BFS_OK) S->error = rc;
-      busy = true;
-    }
-    if (admit && !ge->pending.empty()) busy = true;
-  }
-  // Completions.
+}
+
+// Queries whose results (and host copies) are complete.
+void complete(bfs_server* S, GraphEntry* ge) {
   std::vector<Query*> still;
-  for (Query* q : S->completing) {
+  bool any = false;
+  for (Query* q : ge->completing) {
     const cudaError_t e = cudaEventQuery(q->ev);
     if (e == cudaErrorNotReady) {
       still.push_back(q);
@@ -209,29 +140,110 @@ bool server_pass(bfs_server* S) {
     cudaEventDestroy(q->ev);
     q->ev = nullptr;
     if (e != cudaSuccess) q->status = BFS_ECUDA;
-    if (q->host_out) ges[q->graph]->staging_free.push_back(q->dev_out);
+    if (q->host_out) ge->staging_free.push_back(q->dev_out);
     {
       std::lock_guard<std::mutex> lk(S->mu);
       q->t_done = now_ns();
       q->done = true;
     }
-    S->cv_done.notify_all();
+    any = true;
   }
-  S->completing.swap(still);
-  return busy || !S->completing.empty();
+  ge->completing.swap(still);
+  if (any) S->cv_done.notify_all();
 }
 
-void server_main(bfs_server* S) {
+// Waiting queries into free lanes (they join at the group's next level).
+void admit(bfs_server* S, GraphEntry* ge) {
+  const unsigned long long in_use = ge->grp ? gbfs::serve_group_lanes(ge->grp) : 0ull;
+  std::vector<int> lanes, srcs;
+  std::vector<int*> outs;
+  int next_lane = 0;
+  while (!ge->waiting.empty()) {
+    int lane = -1;
+    for (; next_lane < 64; ++next_lane)
+      if (!((in_use >> next_lane) & 1ull) && ge->lane_q[next_lane] == nullptr) {
+        lane = next_lane++;
+        break;
+      }
+    if (lane < 0) break;
+    Query* q = ge->waiting.front();
+    const size_t nbytes = sizeof(int32_t) * (size_t)ge->g->n;
+    if (!ge->grp) {
+      const size_t need = gbfs::serve_group_bytes(ge->g, S->p.ms_ring);
+      if (!reserve(S, need)) break;
+      const int prio = ge->g->m < (long long)S->p.large_diameter_degree * ge->g->n ? 1 : 0;
+      const int rc = gbfs::serve_group_create(ge->g, S->p.ms_ring, S->p.ms_heavy_min, prio, &ge->grp);
+      if (rc != BFS_OK) {
+        S->error = rc;
+        break;
+      }
+    }
+    if (q->host_out) {
+      if (ge->staging_free.empty()) {
+        if (!reserve(S, nbytes)) break;
+        int32_t* buf = nullptr;
+        if (cudaMalloc(&buf, nbytes) != cudaSuccess) {
+          cudaGetLastError();
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->used -= nbytes;
+          break;
+        }
+        ge->staging_free.push_back(buf);
+        ge->staging_all.push_back(buf);
+      }
+      q->dev_out = ge->staging_free.back();
+      ge->staging_free.pop_back();
+    } else {
+      q->dev_out = q->user_out;
+    }
+    ge->waiting.pop_front();
+    q->lane = lane;
+    q->t_start = now_ns();
+    q->join = gbfs::serve_group_lanes(ge->grp) ? gbfs::serve_group_level(ge->grp) : 0;
+    ge->lane_q[lane] = q;
+    lanes.push_back(lane);
+    srcs.push_back(q->src);
+    outs.push_back(q->dev_out);
+  }
+  if (!lanes.empty()) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->queued -= lanes.size();
+    }
+    const int rc = gbfs::serve_group_join(ge->grp, (int)lanes.size(), lanes.data(), srcs.data(), outs.data());
+    if (rc != BFS_OK) S->error = rc;
+  }
+}
+
+void graph_worker(bfs_server* S, GraphEntry* ge) {
   cudaSetDevice(S->device);
   for (;;) {
-    const bool busy = server_pass(S);
-    std::unique_lock<std::mutex> lk(S->mu);
-    if (S->stop && !busy && S->inbox.empty()) break;
-    if (!busy && S->inbox.empty()) S->cv_work.wait_for(lk, std::chrono::milliseconds(1));
-    else if (busy) {
-      lk.unlock();
-      std::this_thread::yield();
+    bool stopping;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      while (!ge->pending.empty()) {
+        ge->waiting.push_back(ge->pending.front());
+        ge->pending.pop_front();
+      }
+      stopping = S->stop;
     }
+    if (ge->grp && gbfs::serve_group_ready(ge->grp) >= 0) finish_level(S, ge);  // blocks until the level is done
+    complete(S, ge);
+    if (!stopping) admit(S, ge);
+    const bool running = ge->grp && gbfs::serve_group_lanes(ge->grp);
+    if (running) {
+      const int rc = gbfs::serve_group_launch(ge->grp, S->p.tau_inv);
+      if (rc != BFS_OK) S->error = rc;
+      continue;
+    }
+    if (!ge->completing.empty()) {
+      std::this_thread::yield();
+      continue;
+    }
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->stop) break;
+    // Nothing running: sleep until a query arrives (or 1 ms, to retry admission).
+    if (ge->pending.empty()) ge->cv.wait_for(lk, std::chrono::milliseconds(1));
   }
 }
 
@@ -245,7 +257,7 @@ int bfs_serve_create(size_t mem_budget, const bfs_params* params, bfs_server** o
   bfs_server* S = new bfs_server();
   S->budget = mem_budget;
   if (params) S->p = *params; else bfs_params_default(&S->p);
-  if (S->p.ms_ring < 2 || S->p.ms_ring > 8 || S->p.tau_inv < 1) {
+  if (S->p.ms_ring < 2 || S->p.ms_ring > 16 || S->p.tau_inv < 1) {
     delete S;
     return BFS_EINVAL;
   }
@@ -253,7 +265,6 @@ int bfs_serve_create(size_t mem_budget, const bfs_params* params, bfs_server** o
     delete S;
     return BFS_ECUDA;
   }
-  S->th = std::thread(server_main, S);
   *out = S;
   return BFS_OK;
 }
@@ -261,10 +272,12 @@ int bfs_serve_create(size_t mem_budget, const bfs_params* params, bfs_server** o
 int bfs_serve_add_graph(bfs_server* S, bfs_graph* g, int32_t* graph_id) {
   if (!S || !g || !graph_id) return BFS_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) return BFS_EINVAL;
   GraphEntry* ge = new GraphEntry();
   ge->g = g;
   S->graphs.push_back(ge);
   *graph_id = (int32_t)S->graphs.size() - 1;
+  ge->th = std::thread(graph_worker, S, ge);
   return BFS_OK;
 }
 
@@ -274,8 +287,9 @@ int bfs_serve_submit(bfs_server* S, int32_t graph_id, int32_t src, int32_t* dist
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->error.load() != BFS_OK) return S->error.load();
   if (graph_id < 0 || graph_id >= (int32_t)S->graphs.size()) return BFS_ENOTFOUND;
-  if (src < 0 || (int64_t)src >= S->graphs[graph_id]->g->n) return BFS_EINVAL;
-  if (S->inbox.size() >= S->inbox_cap) return BFS_EAGAIN;
+  GraphEntry* ge = S->graphs[graph_id];
+  if (src < 0 || (int64_t)src >= ge->g->n) return BFS_EINVAL;
+  if (S->queued >= S->queue_cap) return BFS_EAGAIN;
   Query* q = new Query();
   q->ticket = S->next_ticket++;
   q->graph = graph_id;
@@ -284,9 +298,10 @@ int bfs_serve_submit(bfs_server* S, int32_t graph_id, int32_t src, int32_t* dist
   q->host_out = host_out;
   q->t_submit = now_ns();
   S->tickets[q->ticket] = q;
-  S->inbox.push_back(q);
+  ge->pending.push_back(q);
+  ++S->queued;
   *ticket = q->ticket;
-  S->cv_work.notify_one();
+  ge->cv.notify_one();
   return BFS_OK;
 }
 
@@ -327,18 +342,22 @@ int bfs_serve_wait(bfs_server* S, uint64_t ticket, int64_t timeout_us, bfs_query
 
 void bfs_serve_destroy(bfs_server* S) {
   if (!S) return;
+  std::vector<GraphEntry*> ges;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
+    ges = S->graphs;
   }
-  S->cv_work.notify_all();
-  if (S->th.joinable()) S->th.join();
+  // Workers finish their running lanes, then exit.
+  for (GraphEntry* ge : ges) ge->cv.notify_all();
+  for (GraphEntry* ge : ges)
+    if (ge->th.joinable()) ge->th.join();
   cudaSetDevice(S->device);
   // Queries never admitted (still queued at shutdown) and completed ones not yet
   // reported are all still registered under their tickets.
-  for (GraphEntry* ge : S->graphs) {
+  for (GraphEntry* ge : ges) {
     gbfs::serve_group_destroy(ge->grp);
-    for (int32_t* b : ge->staging_free) cudaFree(b);
+    for (int32_t* b : ge->staging_all) cudaFree(b);
     delete ge;
   }
   for (auto& kv : S->tickets) delete kv.second;

@@ -49,7 +49,8 @@ def test_rmat_group_sizes(bfs, bits, k):
 @pytest.mark.parametrize("kw", [dict(ms_lanes=64), dict(ms_lanes=7, ms_ring=2), dict(ms_heavy_min=0),
                                 dict(ms_heavy_min=1 << 30), dict(alpha=1, beta=1), dict(alpha=1000, beta=1000),
                                 dict(ms_ring=3, ms_lanes=130), dict(ms_degree_order=1),
-                                dict(ms_degree_order=1, ms_heavy_min=0, ms_lanes=64)])
+                                dict(ms_degree_order=1, ms_heavy_min=0, ms_lanes=64), dict(ms_relabel=0),
+                                dict(ms_relabel=0, ms_degree_order=0, ms_lanes=64, ms_ring=2), dict(ms_ring=16)])
 def test_parameters(bfs, kw):
     rp, col = graphgen.rmat(12, seed=22)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_DEGREE_ORDER)
@@ -74,9 +75,29 @@ def test_large_diameter_many_flushes(bfs):
     rp, col = graphgen.grid2d(70, 90)  # eccentricity up to 158: many ring windows
     g = bfs.bfs_graph_upload(rp, col)
     srcs = graphgen.sources(rp, 70, 2200)
-    for ring in (2, 8):
-        got, st = run_multi(bfs, g, len(rp) - 1, srcs, 8, ms_ring=ring)
+    for ring, relabel in ((2, 1), (8, 1), (16, 1), (5, 0)):
+        got, st = run_multi(bfs, g, len(rp) - 1, srcs, 8, ms_ring=ring, ms_relabel=relabel)
         assert np.array_equal(got, expect(rp, col, srcs, 8))
+    g.free()
+
+
+@pytest.mark.parametrize("rp_bits", [32, 64])
+@pytest.mark.parametrize("degree_order", [False, True])
+def test_renumbered_layout(bfs, rp_bits, degree_order):
+    """The degree-renumbered copy (lists sorted after renumbering, or already in degree order) against the
+    graph as uploaded and the oracle, with isolated vertices among the sources."""
+    rp, col = graphgen.rmat(11, seed=24)
+    rp64 = rp.astype(np.int64)
+    iso = np.flatnonzero(np.diff(rp64) == 0)
+    assert len(iso) >= 4
+    srcs = np.concatenate([graphgen.sources(rp64, 60, 2400), iso[:3], iso[-1:]]).astype(np.int32)
+    g = bfs.bfs_graph_upload(rp.astype(np.int32 if rp_bits == 32 else np.int64), col,
+                             flags=bfs.BFS_DEGREE_ORDER if degree_order else 0)
+    for bits in (8, 32):
+        want = expect(rp64, col, srcs, bits)
+        for relabel in (1, 0):
+            got, _ = run_multi(bfs, g, len(rp) - 1, srcs, bits, ms_relabel=relabel)
+            assert np.array_equal(got, want), (bits, relabel)
     g.free()
 
 
