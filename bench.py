@@ -36,6 +36,7 @@ NSRC = 64
 SRC_SEED = 1002
 METRIC = "GTEPS (harmonic mean, 64 sources) R-MAT s25; BFS queries/s & p99 latency"
 L2_BYTES = 129 * 1024 * 1024
+RELABEL_DEFAULT = 0  # single-source queries on the degree-renumbered copy (bfs_params.relabel)
 
 
 def peaks():
@@ -269,7 +270,7 @@ def run_ours(args):
     t_gen = time.perf_counter() - t_gen
     n, m = len(rp) - 1, len(col)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER))
-    params = bfs.make_params(policy=args.policy, launch=args.launch)
+    params = bfs.make_params(policy=args.policy, launch=args.launch, relabel=args.relabel)
     has_head = m < (1 << 31) - 8  # the library builds the head table when list starts fit int32
     hybrid = not (args.policy == bfs.BFS_POLICY_TD_ONLY or (args.policy == bfs.BFS_POLICY_AUTO and m < 7 * n))
     stream = torch.cuda.Stream()
@@ -323,7 +324,7 @@ def run_ours(args):
     # this workload), and its ratio to the algorithmic bytes of the captured sources.
     traffic, traffic_ratio = None, None
     default_run = (args.scale == SCALE and args.workload == "rmat25" and not args.no_degree_order
-                   and args.policy == 0 and args.launch == 0)
+                   and args.policy == 0 and args.launch == 0 and args.relabel == RELABEL_DEFAULT)
     mt = measured_traffic() if default_run else None
     if mt is not None:
         traffic = mt[0]
@@ -359,6 +360,7 @@ def run_ours(args):
                    "policy": {0: "auto", 1: "frontier", 2: "edges", 3: "td_only"}.get(args.policy, str(args.policy)),
                    "launch": {0: "persistent", 1: "per_level", 2: "graph"}[args.launch],
                    "adjacency_order": "id" if args.no_degree_order else "degree_desc",
+                   "vertex_ids": "degree_renumbered_copy" if args.relabel else "as_uploaded",
                    "l2": "inputs larger than L2 (4.3 GB neighbour ids), no flush",
                    "step": "64 single-source BFS, each timed with CUDA events",
                    "graph_gen_s": round(t_gen, 1)},
@@ -655,6 +657,8 @@ def main(argv=None):
     ap.add_argument("--scale", type=int, default=SCALE)
     ap.add_argument("--policy", type=int, default=0)
     ap.add_argument("--launch", type=int, default=0)
+    ap.add_argument("--relabel", type=int, default=RELABEL_DEFAULT, choices=[0, 1],
+                    help="single-source queries on the degree-renumbered copy of the graph")
     ap.add_argument("--cpu-sample", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-degree-order", action="store_true",

@@ -129,7 +129,12 @@ typedef struct bfs_params {
                                 decreasing degree (1, default; built once per graph on first use and
                                 kept until bfs_graph_free: 4m + 8n bytes plus the row pointers), so the
                                 masks most lists point to share cache lines; 0 = the graph as uploaded */
-    int32_t reserved[1];
+    int32_t relabel;         /* bfs_single: run on the same degree-renumbered copy (1; its head table,
+                                visited mask and a host copy of the id map, 4n bytes, are added on
+                                first use) so the frontier bits of high-degree vertices share cache
+                                lines; distances are still written in the caller's ids.  0 (default):
+                                the graph as uploaded */
+    int32_t reserved[4];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique

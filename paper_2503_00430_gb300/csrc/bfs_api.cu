@@ -197,6 +197,43 @@ int build_head(bfs_graph* g) {
   return BFS_OK;
 }
 
+// Head table and visited mask of the degree-renumbered copy, and its new_of
+// on the host, for single-source queries that run on it.
+int ensure_relabel_single(bfs_graph* g) {
+  int rc = ensure_relabel(g);
+  if (rc != BFS_OK) return rc;
+  Relabel* r = g->rl;
+  if (r->h_new_of) return BFS_OK;
+  const int grid = g->num_sms * 4, block = 256;
+  GBFS_CUDA(cudaMalloc(&r->init_vis, sizeof(unsigned) * (size_t)g->nw));
+  unsigned long long* d_facts = nullptr;
+  GBFS_CUDA(cudaMalloc(&d_facts, 8 * sizeof(unsigned long long)));
+  GBFS_CUDA(cudaMemset(d_facts, 0, 8 * sizeof(unsigned long long)));
+  if (g->rp_bits == 32)
+    k_degree_mask<int><<<grid, block>>>(static_cast<const int*>(r->rp), g->n, g->nw, r->init_vis, d_facts);
+  else
+    k_degree_mask<long long><<<grid, block>>>(static_cast<const long long*>(r->rp), g->n, g->nw, r->init_vis, d_facts);
+  if (g->head) {
+    GBFS_CUDA(cudaMalloc(&r->head, sizeof(int4) * (size_t)g->n));
+    if (g->rp_bits == 32)
+      k_build_head<int><<<grid, block>>>(static_cast<const int*>(r->rp), r->col, g->n, r->head);
+    else
+      k_build_head<long long><<<grid, block>>>(static_cast<const long long*>(r->rp), r->col, g->n, r->head);
+  }
+  GBFS_CUDA(cudaGetLastError());
+  GBFS_CUDA(cudaDeviceSynchronize());
+  cudaFree(d_facts);
+  int* h = static_cast<int*>(malloc(sizeof(int) * (size_t)g->n));
+  if (!h) return BFS_ENOMEM;
+  const cudaError_t e = cudaMemcpy(h, r->new_of, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    free(h);
+    return cuda_fail(e, "cudaMemcpy (new_of)", __FILE__, __LINE__);
+  }
+  r->h_new_of = h;
+  return BFS_OK;
+}
+
 int ensure_single_ws(bfs_graph* g) {
   SingleWs& ws = g->ws;
   if (ws.ready) return BFS_OK;
@@ -257,6 +294,7 @@ static int check_params(const bfs_params& p) {
   if (p.ms_degree_order < 0 || p.ms_degree_order > 1) return BFS_EINVAL;
   if (p.ms_alpha < 1) return BFS_EINVAL;
   if (p.ms_relabel < 0 || p.ms_relabel > 1) return BFS_EINVAL;
+  if (p.relabel < 0 || p.relabel > 1) return BFS_EINVAL;
   return BFS_OK;
 }
 
@@ -387,6 +425,10 @@ int bfs_single_ex(bfs_graph* g, int32_t src, int32_t* dist, const bfs_params* pa
   std::lock_guard<std::mutex> lock(g->mu);
   rc = ensure_single_ws(g);
   if (rc != BFS_OK) return rc;
+  if (p.relabel) {
+    rc = ensure_relabel_single(g);
+    if (rc != BFS_OK) return rc;
+  }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (is_device_pointer(dist)) return run_single(g, src, dist, p, stats, levels, level_cap, s);
   SingleWs& ws = g->ws;

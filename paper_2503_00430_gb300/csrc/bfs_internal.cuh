@@ -75,6 +75,11 @@ struct KParams {
   int need_qv;
   long long timeout_ns;
   int barrier_extra;
+  // Degree-renumbered graph (single-source queries with params->relabel): the
+  // search runs in new ids; dist is written in the caller's ids through these
+  // maps.  Null: the graph as uploaded.
+  const int* new_of = nullptr;   // [n] caller id -> new id (expansion of the level bytes)
+  const int* old_of = nullptr;   // [n] new id -> caller id (direct int32 writes past level 254)
 };
 
 // Direction of level `next_level` (true = top-down), from the counters of the
@@ -147,6 +152,11 @@ struct Relabel {
   int* new_of = nullptr;   // [n] new id of every original vertex
   int* old_of = nullptr;   // [n] original id of every new id
   long long n_live = 0;    // vertices of degree > 0 (they take ids 0 .. n_live-1)
+  // Single-source queries on the copy (built on first use): its head table and
+  // visited mask, and new_of on the host (to map the source).
+  int4* head = nullptr;
+  unsigned* init_vis = nullptr;
+  int* h_new_of = nullptr;
 };
 }
 
@@ -182,6 +192,7 @@ int reorder_by_degree(bfs_graph* g);
 int build_head(bfs_graph* g);
 int vertices_by_degree(bfs_graph* g, int* order);
 int ensure_relabel(bfs_graph* g);  // builds g->rl once (caller holds g->mu)
+int ensure_relabel_single(bfs_graph* g);  // + head table, visited mask, host new_of
 void free_relabel(bfs_graph* g);
 int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);

@@ -88,18 +88,34 @@ struct Mask {
   unsigned long long w[W];
 };
 
+// A four-word mask is one 32-byte sector (every mask array is 32-byte aligned:
+// 32 bytes per vertex from a cudaMalloc base), moved with one 256-bit access,
+// so a scattered gather costs one L1 request instead of two.
+// Masks that a kernel may have changed since it started (X, accumulators, the
+// current frontier inside the persistent serving loop) are loaded through L2
+// (.cg): another SM's atomics and stores are not visible in this SM's L1.
+__device__ __forceinline__ void ld_v4_u64(const unsigned long long* p, Mask<4>& m) {
+  asm volatile("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(m.w[0]), "=l"(m.w[1]), "=l"(m.w[2]), "=l"(m.w[3]) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void ld_nc_v4_u64(const unsigned long long* p, Mask<4>& m) {
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(m.w[0]), "=l"(m.w[1]), "=l"(m.w[2]), "=l"(m.w[3]) : "l"(p));
+}
+__device__ __forceinline__ void st_v4_u64(unsigned long long* p, const Mask<4>& m) {
+  asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(m.w[0]), "l"(m.w[1]), "l"(m.w[2]),
+               "l"(m.w[3]) : "memory");
+}
+
 template <int W>
 __device__ __forceinline__ Mask<W> load_mask(const unsigned long long* p) {
   Mask<W> m;
   if constexpr (W == 4) {
-    const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
-    const ulonglong2 b = reinterpret_cast<const ulonglong2*>(p)[1];
-    m.w[0] = a.x; m.w[1] = a.y; m.w[2] = b.x; m.w[3] = b.y;
+    ld_v4_u64(p, m);
   } else if constexpr (W == 2) {
-    const ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
+    const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2*>(p));
     m.w[0] = a.x; m.w[1] = a.y;
   } else {
-    m.w[0] = p[0];
+    m.w[0] = __ldcg(p);
   }
   return m;
 }
@@ -109,9 +125,7 @@ template <int W>
 __device__ __forceinline__ Mask<W> ldg_mask(const unsigned long long* p) {
   Mask<W> m;
   if constexpr (W == 4) {
-    const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
-    const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
-    m.w[0] = a.x; m.w[1] = a.y; m.w[2] = b.x; m.w[3] = b.y;
+    ld_nc_v4_u64(p, m);
   } else if constexpr (W == 2) {
     const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
     m.w[0] = a.x; m.w[1] = a.y;
@@ -124,8 +138,7 @@ __device__ __forceinline__ Mask<W> ldg_mask(const unsigned long long* p) {
 template <int W>
 __device__ __forceinline__ void store_mask(unsigned long long* p, const Mask<W>& m) {
   if constexpr (W == 4) {
-    reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(m.w[0], m.w[1]);
-    reinterpret_cast<ulonglong2*>(p)[1] = make_ulonglong2(m.w[2], m.w[3]);
+    st_v4_u64(p, m);
   } else if constexpr (W == 2) {
     reinterpret_cast<ulonglong2*>(p)[0] = make_ulonglong2(m.w[0], m.w[1]);
   } else {
@@ -230,8 +243,12 @@ constexpr int kMsPushChunk = 256;
 
 // Plan: one record per frontier vertex with more than kMsPushChunk entries;
 // one packed atomic per warp hands out record slots and chunk tickets in order.
+// Counters another phase of the same level wrote: read through L2 (the
+// persistent serving loop runs several levels in one launch).
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) { return __ldcg(p); }
+
 template <typename RP>
-__global__ void __launch_bounds__(256) k_ms_push_plan(MsArgs A, long long nq) {
+__device__ __forceinline__ void ms_push_plan_body(const MsArgs& A, long long nq) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   for (long long base = tid - (tid & 31); base < nq; base += nth) {
@@ -239,7 +256,7 @@ __global__ void __launch_bounds__(256) k_ms_push_plan(MsArgs A, long long nq) {
     long long s = 0, d = 0;
     int u = 0;
     if (i < nq) {
-      u = A.qcur[i];
+      u = __ldcg(A.qcur + i);
       s = rpv<RP>(A.rp, u);
       d = rpv<RP>(A.rp, (long long)u + 1) - s;
     }
@@ -268,6 +285,21 @@ __global__ void __launch_bounds__(256) k_ms_push_plan(MsArgs A, long long nq) {
       r.v = u;
     }
   }
+}
+
+template <typename RP>
+__global__ void __launch_bounds__(256) k_ms_push_plan(MsArgs A, long long nq) {
+  ms_push_plan_body<RP>(A, nq);
+}
+
+// A chunk record the planning phase wrote (read through L2, see load_mask).
+__device__ __forceinline__ MsHeavy ld_heavy(const MsHeavy* p) {
+  MsHeavy r;
+  r.start = __ldcg(&p->start);
+  r.deg = __ldcg(&p->deg);
+  r.base = __ldcg(&p->base);
+  r.v = __ldcg(&p->v);
+  return r;
 }
 
 // Warp-collective: push the lanes f of one vertex along entries [s, e), 32 per step.
@@ -299,22 +331,70 @@ __device__ __forceinline__ void ms_push_span(const MsArgs& A, const Mask<W>& f, 
   }
 }
 
-// Warp per frontier vertex of at most kMsPushChunk entries, then warp per chunk
-// ticket of the planned vertices (ticket t belongs to the last record whose
-// base is <= t: 32-way search).
+// Frontier vertices with at most kMsThreadPush entries: a thread each, the
+// warp stepping through entry k of its 32 vertices together (large-diameter
+// graphs have thousands of levels of such vertices: a warp per vertex would
+// leave most lanes idle).  Then a warp per frontier vertex of at most
+// kMsPushChunk entries, then a warp per chunk ticket of the planned vertices
+// (ticket t belongs to the last record whose base is <= t: 32-way search).
+constexpr int kMsThreadPush = 8;
+
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
+__device__ __forceinline__ void ms_push_body(const MsArgs& A, long long nq) {
   const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const unsigned lane = ms_lane();
-  const unsigned long long hv = A.ctrl->nheavy;  // written by k_ms_push_plan earlier on this stream
+  const unsigned long long hv = ld_cg_u64(&A.ctrl->nheavy);  // written by the planning phase
   const long long nrec = (long long)(hv & ((1ull << kMsCountBits) - 1)), nch = (long long)(hv >> kMsCountBits);
   unsigned long long edges = 0;
+  {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long base = tid - lane; base < nq; base += nth) {
+      const long long i = base + lane;
+      long long s = 0, d = 0;
+      Mask<W> f;
+      if (i < nq) {
+        const int u = __ldcg(A.qcur + i);
+        s = rpv<RP>(A.rp, u);
+        d = rpv<RP>(A.rp, (long long)u + 1) - s;
+        if (d > kMsThreadPush) d = 0;  // a warp pushes it below
+        else f = load_mask<W>(A.Fcur + (long long)u * W);
+      }
+      edges += (unsigned long long)d;
+      for (int k = 0; k < kMsThreadPush; ++k) {
+        if (!__any_sync(0xffffffffu, k < d)) break;
+        bool touch = false;
+        int v = 0;
+        if (k < d) {
+          v = __ldg(A.col + s + k);
+          const Mask<W> x = load_mask<W>(A.X + (long long)v * W);
+          bool any = false;
+#pragma unroll
+          for (int w = 0; w < W; ++w) {
+            const unsigned long long add = f.w[w] & ~x.w[w];
+            if (add) {
+              atomicOr(A.acc + (long long)v * W + w, add);
+              any = true;
+            }
+          }
+          if (any && !A.dense) {
+            const unsigned bit = 1u << (v & 31);
+            touch = !(atomicOr(A.touched_bm + (v >> 5), bit) & bit);
+          }
+        }
+        if (!A.dense) warp_append(touch, v, &A.ctrl->ntouch, A.touched);
+      }
+    }
+  }
+  edges = warp_sum(edges);
+  if (lane != 0) edges = 0;
   for (long long u0 = gw; u0 < nq + nch; u0 += nwarps) {
     if (u0 < nq) {
-      const int u = A.qcur[u0];
+      const int u = __ldcg(A.qcur + u0);
       const long long s = rpv<RP>(A.rp, u), e = rpv<RP>(A.rp, (long long)u + 1);
-      if (e - s > kMsPushChunk) continue;  // pushed by chunk tickets
+      if (e - s <= kMsThreadPush) continue;  // pushed by its thread above
+      if (e - s > kMsPushChunk) continue;    // pushed by chunk tickets
       if (lane == 0) edges += (unsigned long long)(e - s);
       ms_push_span<W>(A, load_mask<W>(A.Fcur + (long long)u * W), s, e);
     } else {
@@ -323,12 +403,12 @@ __global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
       while (hi - lo > 1) {
         const long long step = (hi - lo + 31) / 32;
         const long long idx = lo + (long long)lane * step;
-        const bool ok = idx < hi && (long long)A.heavy[idx].base <= t;
+        const bool ok = idx < hi && (long long)__ldcg(&A.heavy[idx].base) <= t;
         const unsigned bm = __ballot_sync(0xffffffffu, ok);
         lo += (long long)(31 - __clz(bm)) * step;
         hi = lo + step < hi ? lo + step : hi;
       }
-      const MsHeavy r = A.heavy[lo];
+      const MsHeavy r = ld_heavy(A.heavy + lo);
       const long long cs = r.start + (t - (long long)r.base) * kMsPushChunk;
       const long long ce = cs + (r.deg - (cs - r.start) < kMsPushChunk ? r.deg - (cs - r.start) : kMsPushChunk);
       if (lane == 0) edges += (unsigned long long)(ce - cs);
@@ -338,10 +418,15 @@ __global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
   if (lane == 0 && edges) atomicAdd(&A.ctrl->edges, edges);
 }
 
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_push(MsArgs A, long long nq) {
+  ms_push_body<W, RP>(A, nq);
+}
+
 // ---- apply after push: new lanes of touched vertices ----
 template <int W, typename RP>
-__global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
-  const long long nt = (long long)A.ctrl->ntouch;  // written by k_ms_push earlier on this stream
+__device__ __forceinline__ void ms_apply_body(const MsArgs& A) {
+  const long long nt = (long long)ld_cg_u64(&A.ctrl->ntouch);  // written by the push phase
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long nf = 0, mf = 0, dd = 0;
@@ -357,7 +442,7 @@ __global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
 #pragma unroll
     for (int k = 0; k < W; ++k) nn.w[k] = 0;
     if (in) {
-      v = A.touched[i];
+      v = __ldcg(A.touched + i);
       Mask<W> a = load_mask<W>(A.acc + (long long)v * W);
       Mask<W> x = load_mask<W>(A.X + (long long)v * W);
       Mask<W> z;
@@ -392,6 +477,11 @@ __global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
     if (mf) atomicAdd(&A.ctrl->mf, mf);
     if (dd) atomicAdd(&A.ctrl->done_deg, dd);
   }
+}
+
+template <int W, typename RP>
+__global__ void __launch_bounds__(256) k_ms_apply(MsArgs A) {
+  ms_apply_body<W, RP>(A);
 }
 
 // ---- apply after a dense push: every vertex, in id order (coalesced) ----
@@ -722,11 +812,13 @@ __global__ void __launch_bounds__(256) k_ms_heavy_apply(MsArgs A) {
   }
 }
 
-__global__ void k_ms_zero(unsigned long long* p, long long count) {
+__device__ __forceinline__ void ms_zero_body(unsigned long long* p, long long count) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   for (long long i = tid; i < count; i += nth) p[i] = 0ull;
 }
+
+__global__ void k_ms_zero(unsigned long long* p, long long count) { ms_zero_body(p, count); }
 
 // ---- writer: ring levels [l0, l0 + nlev) into dist[i][v] ----
 // A block owns a tile of 128 vertices (caller's ids).
@@ -791,6 +883,11 @@ __global__ void __launch_bounds__(256) k_ms_write(const unsigned long long* F, c
       }
       if (!first && f) atomicOr(&tile_or[ww], f);
       const int js = j ^ (8 * ww);
+      if (f == 0) {  // no lane found: every entry "unreached"
+#pragma unroll
+        for (int k = 0; k < 16; ++k) code[ww][k][js] = 0xffffffffu;
+        continue;
+      }
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const unsigned sf = spread4((unsigned)(f >> (4 * k)) & 0xfu);
@@ -1140,6 +1237,14 @@ int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, co
 // ============================================================================
 namespace gbfs {
 
+// State of one persistent serving launch (zeroed before it starts).
+struct ServeLoop {
+  unsigned long long barrier;   // grid-barrier arrivals
+  int status;                   // BFS_OK or BFS_ETIMEOUT
+  int levels;                   // levels the launch completed
+  MsCtrl ctrl[2];               // counters of the launch's even / odd levels
+};
+
 struct ServeGroup {
   bfs_graph* g = nullptr;
   int ring = 8;
@@ -1165,11 +1270,22 @@ struct ServeGroup {
   int* h_newlane = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_level = nullptr;
+  // Blocks per launch.  A high-priority group gets the usual grid; the others
+  // get about one block per 2048 vertices, so each block is short-lived and
+  // the priority group's kernels find free SM slots between them instead of
+  // waiting for a grid-stride kernel to end.
+  int grid = 0, wgrid = 0;
   int L = 0, qc = 0, flushed = 0;
   long long nf = 0;
   long long mf = 0;        // degree sum of the current frontier (an upper bound after joins)
   unsigned long long lanes = 0, act = 0, first = 0;
   bool launched = false;
+  // Large-diameter groups run consecutive push levels in one persistent launch.
+  bool use_loop = false;
+  bool loop_launched = false;
+  int loop_grid = 0;
+  ServeLoop* SL = nullptr;      // device
+  ServeLoop* h_SL = nullptr;    // pinned mirror
 };
 
 namespace {
@@ -1210,8 +1326,13 @@ __global__ void __launch_bounds__(256) k_serve_write(const unsigned long long* F
       const long long v = v0 + j;
       unsigned long long f = 0, p0 = 0, p1 = 0, p2 = 0, p3 = 0;
       if (v < n) {
-        for (int l = nlev - 1; l >= 0; --l) {
-          const unsigned long long m = F[(long long)((l0 + l) % ring) * n + v] & vmask[l];
+        // All of the window's loads in flight at once, then the planes.
+        unsigned long long mm[kMsMaxRing];
+#pragma unroll
+        for (int l = 0; l < kMsMaxRing; ++l) mm[l] = l < nlev ? F[(long long)((l0 + l) % ring) * n + v] & vmask[l] : 0ull;
+#pragma unroll
+        for (int l = kMsMaxRing - 1; l >= 0; --l) {
+          const unsigned long long m = mm[l];
           f |= m;
           p0 = (p0 & ~m) | ((l & 1) ? m : 0ull);
           p1 = (p1 & ~m) | ((l & 2) ? m : 0ull);
@@ -1251,8 +1372,7 @@ __global__ void __launch_bounds__(256) k_serve_write(const unsigned long long* F
   }
 }
 
-template <typename RP>
-void serve_step(ServeGroup* G, bool push) {
+MsArgs serve_args(const ServeGroup* G) {
   MsArgs A{};
   A.rp = G->g->rp;
   A.col = G->g->col;
@@ -1275,7 +1395,105 @@ void serve_step(ServeGroup* G, bool push) {
   A.ctrl = G->ctrl;
   A.heavy_min = G->heavy_min;
   A.want_queue = 1;
-  ms_step<1, RP>(A, push, false, G->nf, G->mf, A.Fnext, G->n, G->g->num_sms * 8, G->stream);
+  return A;
+}
+
+template <typename RP>
+void serve_step(ServeGroup* G, bool push) {
+  const MsArgs A = serve_args(G);
+  ms_step<1, RP>(A, push, false, G->nf, G->mf, A.Fnext, G->n, G->grid, G->stream);
+}
+
+// Grid barrier of the persistent serving launch: arrival with a release add,
+// a bounded acquire spin; on timeout the status is set and every block returns.
+__device__ bool loop_barrier(ServeLoop* SL, unsigned& epoch, long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&SL->barrier) : "memory");
+    int ok = 1;
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    for (;;) {
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(&SL->barrier) : "memory");
+      if (v >= target) break;
+      if (*reinterpret_cast<volatile int*>(&SL->status) != 0) {
+        ok = 0;
+        break;
+      }
+      if ((++spins & 63u) == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t0 == 0) {
+          t0 = t;
+        } else if ((long long)(t - t0) > timeout_ns) {
+          atomicCAS(&SL->status, 0, BFS_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && *reinterpret_cast<volatile int*>(&SL->status) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Consecutive push levels of a 64-lane serving group in one cooperative
+// launch (the same phases as the per-level launches, grid barriers between
+// them).  It stops after the level at which a lane's frontier empties (the
+// host retires it), when the frontier is empty or dense enough for a pull,
+// or after max_levels levels (the frontier ring must be flushed).  Frontier
+// masks change between levels of the launch, so they are read with coherent
+// loads only.
+template <typename RP>
+__global__ void __launch_bounds__(256) k_serve_loop(MsArgs A, unsigned long long* F, int ring, int L0, int* q0,
+                                                    int* q1, int qc0, long long nf0, long long mf0, int max_levels,
+                                                    int tau_inv, long long timeout_ns, int need_plan, ServeLoop* SL) {
+  unsigned epoch = 0;
+  const unsigned long long lanes = A.full[0];
+  unsigned long long act = A.act[0];
+  long long nf = nf0;
+  int L = L0, qc = qc0;
+  (void)mf0;
+  for (int it = 0;;) {
+    MsCtrl* C = &SL->ctrl[it & 1];
+    A.ctrl = C;
+    A.Fcur = F + (long long)(L % ring) * A.n;
+    A.Fnext = F + (long long)((L + 1) % ring) * A.n;
+    A.qcur = qc ? q1 : q0;
+    A.qnext = qc ? q0 : q1;
+    A.act[0] = act;
+    ms_zero_body(A.Fnext, A.n);
+    if (need_plan) ms_push_plan_body<RP>(A, nf);  // only vertices of more than kMsPushChunk entries
+    if (!loop_barrier(SL, epoch, timeout_ns)) return;
+    ms_push_body<1, RP>(A, nf);
+    if (!loop_barrier(SL, epoch, timeout_ns)) return;
+    ms_apply_body<1, RP>(A);
+    if (!loop_barrier(SL, epoch, timeout_ns)) return;
+    const long long nf2 = (long long)ld_cg_u64(&C->nf);
+    const unsigned long long act2 = ld_cg_u64(&C->act[0]) & lanes;
+    ++it;
+    if (nf2 == 0 || act2 != lanes || it >= max_levels || !((long long)tau_inv * nf2 < A.n)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) SL->levels = it;
+      return;
+    }
+    // Counters of the next level: the slot used two levels ago, which every
+    // block has finished reading (they all passed this level's barriers).
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      unsigned long long* z = reinterpret_cast<unsigned long long*>(&SL->ctrl[it & 1]);
+      for (int k = 0; k < (int)(sizeof(MsCtrl) / sizeof(unsigned long long)); ++k) z[k] = 0ull;
+    }
+    L += 1;
+    qc ^= 1;
+    nf = nf2;
+    act = act2;
+  }
 }
 
 int serve_flush(ServeGroup* G, int upto) {
@@ -1290,7 +1508,7 @@ int serve_flush(ServeGroup* G, int upto) {
       if (((G->lanes >> i) & 1ull) && G->h_join[i] <= G->flushed + l) valid[l] |= 1ull << i;
   unsigned long long* d_valid = reinterpret_cast<unsigned long long*>(G->ctrl + 1);
   GBFS_CUDA(cudaMemcpyAsync(d_valid, valid, sizeof(valid), cudaMemcpyHostToDevice, G->stream));
-  k_serve_write<<<G->g->num_sms * 8, 256, 0, G->stream>>>(G->F, G->n, G->ring, G->flushed, nlev, d_valid, G->lanes,
+  k_serve_write<<<G->wgrid, 256, 0, G->stream>>>(G->F, G->n, G->ring, G->flushed, nlev, d_valid, G->lanes,
                                                            G->first, G->d_out, G->d_join);
   GBFS_CUDA(cudaGetLastError());
   G->first &= ~G->lanes;
@@ -1313,6 +1531,12 @@ int serve_group_create(bfs_graph* g, int ring, int heavy_min, int high_priority,
   G->n = g->n;
   G->heavy_min = heavy_min;
   const size_t n = (size_t)g->n;
+  {
+    const long long base = (long long)g->num_sms * 8;
+    const long long many = ((long long)n + 2047) / 2048, tiles = ((long long)n + kWt - 1) / kWt / 4;
+    G->grid = (int)(high_priority ? base : std::min(std::max(base, many), 1ll << 20));
+    G->wgrid = (int)(high_priority ? base : std::min(std::max(base, tiles), 1ll << 20));
+  }
   int rc = BFS_OK;
   do {
     cudaError_t e = cudaMalloc(&G->X, 8 * n);
@@ -1343,6 +1567,19 @@ int serve_group_create(bfs_graph* g, int ring, int heavy_min, int high_priority,
     if (e == cudaSuccess)
       e = cudaStreamCreateWithPriority(&G->stream, cudaStreamNonBlocking, high_priority ? prio_hi : prio_lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->ev_level, cudaEventDisableTiming);
+    if (e == cudaSuccess && high_priority) {
+      // Persistent push levels: all blocks must be resident at once (cooperative launch).
+      e = cudaMalloc(&G->SL, sizeof(ServeLoop));
+      if (e == cudaSuccess) e = cudaMallocHost(&G->h_SL, sizeof(ServeLoop));
+      int per_sm = 0;
+      const void* fn = g->rp_bits == 32 ? reinterpret_cast<const void*>(&k_serve_loop<int>)
+                                        : reinterpret_cast<const void*>(&k_serve_loop<long long>);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+      if (e == cudaSuccess && per_sm >= 1) {
+        G->loop_grid = std::min(per_sm, 2) * g->num_sms;
+        G->use_loop = true;
+      }
+    }
     if (e != cudaSuccess) { rc = cuda_fail(e, "serving group allocation", __FILE__, __LINE__); break; }
     rc = vertices_by_degree(g, G->order);
   } while (0);
@@ -1377,6 +1614,8 @@ void serve_group_destroy(ServeGroup* G) {
   if (G->h_new) cudaFreeHost(G->h_new);
   if (G->h_newlane) cudaFreeHost(G->h_newlane);
   if (G->ev_level) cudaEventDestroy(G->ev_level);
+  cudaFree(G->SL);
+  if (G->h_SL) cudaFreeHost(G->h_SL);
   if (G->stream) cudaStreamDestroy(G->stream);
   delete G;
 }
@@ -1387,7 +1626,7 @@ int serve_group_level(const ServeGroup* G) { return G->L; }
 
 int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* srcs, int* const* outs) {
   if (count <= 0) return BFS_OK;
-  const int grid = G->g->num_sms * 8;
+  const int grid = G->grid;
   unsigned long long mask = 0;
   for (int k = 0; k < count; ++k) mask |= 1ull << lanes_idx[k];
   if (G->lanes == 0) {
@@ -1434,9 +1673,29 @@ int serve_group_launch(ServeGroup* G, int tau_inv) {
     if (rc != BFS_OK) return rc;
   }
   const bool push = (long long)tau_inv * G->nf < G->n;
-  if (G->g->rp_bits == 32) serve_step<int>(G, push); else serve_step<long long>(G, push);
-  GBFS_CUDA(cudaGetLastError());
-  GBFS_CUDA(cudaMemcpyAsync(G->h_ctrl, G->ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, G->stream));
+  if (G->use_loop && push) {
+    // As many push levels as the ring has room for, in one launch.
+    MsArgs A = serve_args(G);
+    unsigned long long* F = G->F;
+    int ring = G->ring, L0 = G->L, qc0 = G->qc, max_levels = G->ring - 1 - (G->L - G->flushed);
+    int* q0 = G->q[0];
+    int* q1 = G->q[1];
+    long long nf0 = G->nf, mf0 = G->mf, timeout_ns = 10000000000ll;
+    ServeLoop* SL = G->SL;
+    int need_plan = G->g->max_deg > kMsPushChunk ? 1 : 0;
+    void* args[] = {&A,  &F,          &ring,    &L0,         &q0,        &q1, &qc0,
+                    &nf0, &mf0,       &max_levels, &tau_inv, &timeout_ns, &need_plan, &SL};
+    GBFS_CUDA(cudaMemsetAsync(G->SL, 0, sizeof(ServeLoop), G->stream));
+    const void* fn = G->g->rp_bits == 32 ? reinterpret_cast<const void*>(&k_serve_loop<int>)
+                                         : reinterpret_cast<const void*>(&k_serve_loop<long long>);
+    GBFS_CUDA(cudaLaunchCooperativeKernel(fn, dim3((unsigned)G->loop_grid), dim3(256), args, 0, G->stream));
+    GBFS_CUDA(cudaMemcpyAsync(G->h_SL, G->SL, sizeof(ServeLoop), cudaMemcpyDeviceToHost, G->stream));
+    G->loop_launched = true;
+  } else {
+    if (G->g->rp_bits == 32) serve_step<int>(G, push); else serve_step<long long>(G, push);
+    GBFS_CUDA(cudaGetLastError());
+    GBFS_CUDA(cudaMemcpyAsync(G->h_ctrl, G->ctrl, sizeof(MsCtrl), cudaMemcpyDeviceToHost, G->stream));
+  }
   GBFS_CUDA(cudaEventRecord(G->ev_level, G->stream));
   G->launched = true;
   return BFS_OK;
@@ -1455,7 +1714,17 @@ int serve_group_finish(ServeGroup* G, unsigned long long* retired) {
   if (!G->launched) return BFS_OK;
   GBFS_CUDA(cudaEventSynchronize(G->ev_level));
   G->launched = false;
-  const MsCtrl c = *G->h_ctrl;
+  MsCtrl c = *G->h_ctrl;
+  if (G->loop_launched) {
+    // The launch ran levels L .. L+k-1; continue as after a single step at L+k-1.
+    G->loop_launched = false;
+    if (G->h_SL->status != BFS_OK) return G->h_SL->status;
+    const int k = G->h_SL->levels;
+    if (k < 1) return BFS_ECUDA;
+    c = G->h_SL->ctrl[(k - 1) & 1];
+    G->L += k - 1;
+    G->qc ^= (k - 1) & 1;
+  }
   const unsigned long long act_next = c.act[0] & G->lanes;
   const unsigned long long done = G->lanes & ~act_next;
   G->nf = (long long)c.nf;

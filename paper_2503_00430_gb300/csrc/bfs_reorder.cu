@@ -7,6 +7,7 @@
 // (CUDA toolkit source library); no BFS kernel uses CUB.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
@@ -229,6 +230,9 @@ int ensure_relabel(bfs_graph* g) {
 
 void free_relabel(bfs_graph* g) {
   if (!g->rl) return;
+  cudaFree(g->rl->head);
+  cudaFree(g->rl->init_vis);
+  free(g->rl->h_new_of);
   cudaFree(g->rl->rp);
   cudaFree(g->rl->col);
   cudaFree(g->rl->new_of);

@@ -112,7 +112,7 @@ __device__ __forceinline__ int4 ldg4_first(const int* p) {
 // The level of vertex v is L + 1: a level byte while the search keeps them
 // (direct = false), else its int32 distance.
 __device__ __forceinline__ void mark_level(const KParams& P, bool direct, int v, int L) {
-  if (direct) P.dist[v] = L + 1;
+  if (direct) P.dist[P.old_of ? P.old_of[v] : v] = L + 1;
   else st_u8_last(P.lv8 + v, (unsigned)(L + 1));
 }
 
@@ -269,11 +269,32 @@ __device__ __noinline__ void init_phase(const KParams& P) {
 }
 
 // dist[v] = level byte of v, or -1 where it is 255 (every vertex written).
+// On a renumbered graph the byte of caller vertex v is at new_of[v]; a
+// vertex of degree 0 (new id >= n_live) other than the source is unreached.
 __device__ __noinline__ void expand_phase(const KParams& P) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long n = P.n;
   long long done = 0;
+  if (P.new_of) {
+    auto level_of = [&](int nv) -> int {
+      if ((long long)nv >= P.n_live && nv != P.src) return -1;
+      const int t = P.lv8[nv];
+      return t == 255 ? -1 : t;
+    };
+    if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
+      const long long n4 = n >> 2;
+      const int4* m4 = reinterpret_cast<const int4*>(P.new_of);
+      int4* d4 = reinterpret_cast<int4*>(P.dist);
+      for (long long i = tid; i < n4; i += nth) {
+        const int4 a = __ldcs(m4 + i);
+        __stcs(d4 + i, make_int4(level_of(a.x), level_of(a.y), level_of(a.z), level_of(a.w)));
+      }
+      done = n4 << 2;
+    }
+    for (long long i = done + tid; i < n; i += nth) P.dist[i] = level_of(P.new_of[i]);
+    return;
+  }
   if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
     const long long n4 = n >> 2;
     const unsigned* l4 = reinterpret_cast<const unsigned*>(P.lv8);
@@ -1347,14 +1368,17 @@ static int resolve_policy(const bfs_graph* g, const bfs_params& p) {
 
 static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, KParams& K) {
   SingleWs& ws = g->ws;
-  K.rp = g->rp;
-  K.col = g->col;
+  const Relabel* rl = (p.relabel && g->rl && g->rl->h_new_of) ? g->rl : nullptr;
+  K.rp = rl ? rl->rp : g->rp;
+  K.col = rl ? rl->col : g->col;
   K.n = g->n;
   K.m = g->m;
   K.nw = g->nw;
-  K.src = src;
-  K.init_vis = g->init_vis;
-  K.head = g->head;
+  K.src = rl ? rl->h_new_of[src] : src;
+  K.init_vis = rl ? rl->init_vis : g->init_vis;
+  K.head = rl ? rl->head : g->head;
+  K.new_of = rl ? rl->new_of : nullptr;
+  K.old_of = rl ? rl->old_of : nullptr;
   K.lv8 = ws.lv8;
   K.n_live = g->n - g->isolated;
   K.dist = dist;

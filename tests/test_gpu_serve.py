@@ -111,3 +111,16 @@ def test_errors(bfs, graphs):
         srv.poll(t)
     assert e.value.code == bfs.BFS_ENOTFOUND
     srv.destroy()
+
+
+@pytest.mark.parametrize("ring", [16, 3])
+def test_persistent_push_levels_large_diameter(bfs, ring):
+    """A large-diameter graph runs many push levels per persistent launch (every level a push with
+    tau_inv=1); lanes retire and join between launches; every query's distances are the oracle's."""
+    rp, col = graphgen.grid2d(30, 90)
+    g = bfs.bfs_graph_upload(rp, col)
+    gs = [(rp, col)]
+    for rep in range(2):
+        qs = [(0, int(s)) for s in graphgen.sources(rp, 200, 4000 + rep)]
+        run_mix(bfs, gs, [g], qs, tau_inv=1, ms_ring=ring)
+    g.free()

@@ -231,3 +231,29 @@ def test_level_records_without_counters(bfs, launch):
         if launch != 1:
             assert all(x["ns"] > 0 for x in lv1)
     g.free()
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_renumbered_copy(bfs, bits):
+    """params.relabel: the search runs on the degree-renumbered copy (lists highest degree first), so the
+    distances are the oracle's and the counters those of the degree-ordered layout, in every launch mode;
+    a graph uploaded in caller order (lists sorted after renumbering) and isolated sources too."""
+    rp, col = graphgen.rmat(14, seed=12)
+    iso = [int(v) for v in np.flatnonzero(np.diff(rp) == 0)[:1]]
+    srcs = [int(s) for s in graphgen.sources(rp, 3, 1011)] + iso
+    check(bfs, rp, col, srcs, rp_bits=bits, degree_order=True, launches=(0, 1, 2), extra=dict(relabel=1))
+    g = bfs.bfs_graph_upload(rp, col, row_ptr_bits=bits)
+    n = len(rp) - 1
+    for src in srcs:
+        got, _, _ = run(bfs, g, src, n, relabel=1)
+        assert np.array_equal(got, oracle.bfs(rp, col, src)), src
+    g.free()
+
+
+def test_renumbered_copy_deep_search(bfs):
+    """More than 254 levels on the renumbered copy: distances past the level bytes are written through the
+    new-to-caller id map."""
+    for rp, col in (G.path_graph(600), graphgen.grid2d(3, 400)):
+        n = len(rp) - 1
+        check(bfs, rp, col, [0, n // 3, n - 1], policies={k: POLICIES[k] for k in ("auto", "edges")},
+              launches=(0, 1), extra=dict(relabel=1), check_stats=False)
