@@ -36,7 +36,7 @@ NSRC = 64
 SRC_SEED = 1002
 METRIC = "GTEPS (harmonic mean, 64 sources) R-MAT s25; BFS queries/s & p99 latency"
 L2_BYTES = 129 * 1024 * 1024
-RELABEL_DEFAULT = 0  # single-source queries on the degree-renumbered copy (bfs_params.relabel)
+RELABEL_DEFAULT = 1  # single-source queries on the degree-renumbered copy (bfs_params.relabel)
 
 
 def peaks():

@@ -350,7 +350,7 @@ typedef struct bfs_query_stats {
 } bfs_query_stats;
 
 /*
- * Start a server thread on the current device.  The server runs the queries
+ * Start a server on the current device.  The server runs the queries
  * of each registered graph in one 64-lane multi-source group (Section 2's
  * level-synchronous loop for all lanes at once); a query waiting for a lane
  * joins the running group at its next level and leaves when its frontier is
@@ -358,8 +358,13 @@ typedef struct bfs_query_stats {
  * batching).  Admission is bounded by mem_budget bytes of device memory: a
  * graph's group state (about (8*(2+ms_ring) + 16) bytes per vertex) when its
  * first query arrives, and a 4n-byte staging buffer for every running query
- * whose output is host memory.  Uses params->ms_ring, ms_heavy_min and tau_inv
- * (levels run push when tau_inv * |F| < n, else pull).  NULL params = defaults.
+ * whose output is host memory.  Uses params->ms_ring, ms_heavy_min, tau_inv
+ * (levels run push when tau_inv * |F| < n, else pull) and large_diameter_degree:
+ * a graph with m < large_diameter_degree * n (Section 3's large-diameter class)
+ * gets a high-priority stream, writes each distance as it is found, and runs
+ * consecutive push levels in one persistent launch (bounded device waits:
+ * BFS_ETIMEOUT if one runs out).  Every graph has its own worker thread.
+ * NULL params = defaults.
  */
 int bfs_serve_create(size_t mem_budget, const bfs_params *params, bfs_server **out);
 
@@ -369,7 +374,9 @@ int bfs_serve_add_graph(bfs_server *srv, bfs_graph *g, int32_t *graph_id);
 /*
  * Queue the query (graph_id, src).  dist_out: int32[n], device or host memory
  * (detected; pinned host memory avoids a synchronous copy), owned by the caller
- * and valid until the query is reported done.  Returns a ticket.
+ * and valid until the query is reported done.  The server writes it on its own
+ * streams, which are not ordered with the caller's: device work that writes
+ * the buffer must have completed before the call.  Returns a ticket.
  * Errors: BFS_EINVAL, BFS_ENOTFOUND (graph id), BFS_EAGAIN (queue full).
  */
 int bfs_serve_submit(bfs_server *srv, int32_t graph_id, int32_t src, int32_t *dist_out, uint64_t *ticket);
@@ -382,7 +389,7 @@ int bfs_serve_poll(bfs_server *srv, uint64_t ticket, int *done, bfs_query_stats 
  * Returns BFS_ETIMEOUT if the limit passes first (the query keeps running). */
 int bfs_serve_wait(bfs_server *srv, uint64_t ticket, int64_t timeout_us, bfs_query_stats *stats);
 
-/* Finish running queries, drop queued ones, stop the thread, free the server. */
+/* Finish running queries, drop queued ones, stop the threads, free the server. */
 void bfs_serve_destroy(bfs_server *srv);
 
 /*

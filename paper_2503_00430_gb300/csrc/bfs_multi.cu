@@ -168,6 +168,12 @@ struct MsArgs {
   int heavy_min;               // pull: vertices with more entries go to the warp-cooperative pass
   int dense;                   // push: no touched list; the apply pass scans every vertex
   int want_queue;              // pull / dense apply: also append the new frontier's vertices to qnext
+  // Serving groups that write distances as they are found (large-diameter
+  // graphs): lane i's row is out[i], its level 0 is join[i]; out_level is the
+  // level being found (L + 1).  Null out: rows are written from the ring.
+  int* const* out;
+  const int* join;
+  int out_level;
 };
 
 template <int W>
@@ -196,6 +202,20 @@ __device__ __forceinline__ void warp_or_active(const Mask<W>& nn, MsCtrl* ctrl) 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t |= __shfl_xor_sync(0xffffffffu, t, o);
     if ((threadIdx.x & 31u) == 0 && t) atomicOr(&ctrl->act[k], t);
+  }
+}
+
+// Lane i in nn found v at out_level: its distance is out_level - join[i].
+template <int W>
+__device__ __forceinline__ void direct_out(const MsArgs& A, long long v, const Mask<W>& nn) {
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    unsigned long long b = nn.w[k];
+    while (b) {
+      const int i = 64 * k + __ffsll((long long)b) - 1;
+      b &= b - 1;
+      A.out[i][v] = A.out_level - A.join[i];
+    }
   }
 }
 
@@ -458,6 +478,7 @@ __device__ __forceinline__ void ms_apply_body(const MsArgs& A) {
       atomicAnd(A.touched_bm + (v >> 5), ~(1u << (v & 31)));
       nz = !is_zero<W>(nn);
       if (nz) {
+        if (A.out) direct_out<W>(A, v, nn);
         const long long d = rpv<RP>(A.rp, (long long)v + 1) - rpv<RP>(A.rp, v);
         nf += 1;
         mf += (unsigned long long)d;
@@ -513,6 +534,7 @@ __global__ void __launch_bounds__(256) k_ms_apply_dense(MsArgs A) {
         store_mask<W>(A.acc + v * W, z);
         nz = !is_zero<W>(nn);
         if (nz) {
+          if (A.out) direct_out<W>(A, v, nn);
           store_mask<W>(A.X + v * W, x);
           store_mask<W>(A.Fnext + v * W, nn);  // Fnext was zeroed before the push
           const long long d = rpv<RP>(A.rp, v + 1) - rpv<RP>(A.rp, v);
@@ -613,6 +635,7 @@ __global__ void __launch_bounds__(256, GBFS_MS_PULL_MINB) k_ms_pull(MsArgs A) {
           }
           nz = !is_zero<W>(nn);
           if (nz) {
+            if (A.out) direct_out<W>(A, v, nn);
             store_mask<W>(A.X + v * W, x);
             nf += 1;
             mf += (unsigned long long)(e - s);
@@ -791,6 +814,7 @@ __global__ void __launch_bounds__(256) k_ms_heavy_apply(MsArgs A) {
       store_mask<W>(A.Fnext + v * W, nn);
       nz = !is_zero<W>(nn);
       if (nz) {
+        if (A.out) direct_out<W>(A, v, nn);
         store_mask<W>(A.X + v * W, x);
         nf += 1;
         mf += (unsigned long long)r.deg;
@@ -1280,7 +1304,9 @@ struct ServeGroup {
   long long mf = 0;        // degree sum of the current frontier (an upper bound after joins)
   unsigned long long lanes = 0, act = 0, first = 0;
   bool launched = false;
-  // Large-diameter groups run consecutive push levels in one persistent launch.
+  // Large-diameter groups write distances as they are found (no ring flush)
+  // and run consecutive push levels in one persistent launch.
+  bool direct = false;
   bool use_loop = false;
   bool loop_launched = false;
   int loop_grid = 0;
@@ -1304,6 +1330,18 @@ __global__ void k_serve_seed(unsigned long long* X, unsigned long long* Fcur, in
     atomicOr(X + s, bit);
     atomicOr(Fcur + s, bit);
     q[nf + k] = s;
+  }
+}
+
+// Direct-output groups: the joining lanes' rows start as "unreached" with 0
+// at their sources.
+__global__ void k_serve_init_rows(int* const* out, const int* lane, const int* src, int count, long long n) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  for (long long t = tid; t < (long long)count * n; t += nth) {
+    const int k = (int)(t / n);
+    const long long v = t - (long long)k * n;
+    out[lane[k]][v] = v == (long long)src[k] ? 0 : -1;
   }
 }
 
@@ -1395,6 +1433,11 @@ MsArgs serve_args(const ServeGroup* G) {
   A.ctrl = G->ctrl;
   A.heavy_min = G->heavy_min;
   A.want_queue = 1;
+  if (G->direct) {
+    A.out = G->d_out;
+    A.join = G->d_join;
+    A.out_level = G->L + 1;
+  }
   return A;
 }
 
@@ -1469,6 +1512,7 @@ __global__ void __launch_bounds__(256) k_serve_loop(MsArgs A, unsigned long long
     A.qcur = qc ? q1 : q0;
     A.qnext = qc ? q0 : q1;
     A.act[0] = act;
+    A.out_level = L + 1;
     ms_zero_body(A.Fnext, A.n);
     if (need_plan) ms_push_plan_body<RP>(A, nf);  // only vertices of more than kMsPushChunk entries
     if (!loop_barrier(SL, epoch, timeout_ns)) return;
@@ -1497,6 +1541,10 @@ __global__ void __launch_bounds__(256) k_serve_loop(MsArgs A, unsigned long long
 }
 
 int serve_flush(ServeGroup* G, int upto) {
+  if (G->direct) {  // rows were written as the levels ran
+    G->flushed = upto + 1;
+    return BFS_OK;
+  }
   const int nlev = upto - G->flushed + 1;
   if (nlev <= 0 || !G->lanes) {
     G->flushed = upto + 1;
@@ -1579,6 +1627,7 @@ int serve_group_create(bfs_graph* g, int ring, int heavy_min, int high_priority,
         G->loop_grid = std::min(per_sm, 2) * g->num_sms;
         G->use_loop = true;
       }
+      G->direct = true;
     }
     if (e != cudaSuccess) { rc = cuda_fail(e, "serving group allocation", __FILE__, __LINE__); break; }
     rc = vertices_by_degree(g, G->order);
@@ -1655,6 +1704,11 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
                             G->stream));
   GBFS_CUDA(cudaMemcpyAsync(G->d_join, G->h_join, sizeof(int) * 64, cudaMemcpyHostToDevice, G->stream));
   GBFS_CUDA(cudaMemcpyAsync(G->d_out, G->h_out, sizeof(int*) * 64, cudaMemcpyHostToDevice, G->stream));
+  if (G->direct) {
+    const long long total = (long long)count * G->n;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)G->g->num_sms * 32);
+    k_serve_init_rows<<<blocks, 256, 0, G->stream>>>(G->d_out, G->d_newlane, G->d_new, count, G->n);
+  }
   k_serve_seed<<<1, 64, 0, G->stream>>>(G->X, G->F + (long long)(G->L % G->ring) * G->n, G->q[G->qc], G->nf, G->d_new,
                                         G->d_newlane, count);
   GBFS_CUDA(cudaGetLastError());
@@ -1668,7 +1722,7 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
 
 int serve_group_launch(ServeGroup* G, int tau_inv) {
   if (!G->lanes || G->launched) return BFS_OK;
-  if (G->L + 1 - G->flushed >= G->ring) {
+  if (!G->direct && G->L + 1 - G->flushed >= G->ring) {
     const int rc = serve_flush(G, G->L);
     if (rc != BFS_OK) return rc;
   }
@@ -1677,7 +1731,11 @@ int serve_group_launch(ServeGroup* G, int tau_inv) {
     // As many push levels as the ring has room for, in one launch.
     MsArgs A = serve_args(G);
     unsigned long long* F = G->F;
-    int ring = G->ring, L0 = G->L, qc0 = G->qc, max_levels = G->ring - 1 - (G->L - G->flushed);
+    // Ring-writer groups stop when the ring is full; direct-output groups stop
+    // at a retirement, or after 64 levels while lanes are free (queries that
+    // arrive meanwhile join at the next launch).
+    int ring = G->ring, L0 = G->L, qc0 = G->qc;
+    int max_levels = G->direct ? (G->lanes == ~0ull ? 4096 : 64) : G->ring - 1 - (G->L - G->flushed);
     int* q0 = G->q[0];
     int* q1 = G->q[1];
     long long nf0 = G->nf, mf0 = G->mf, timeout_ns = 10000000000ll;

@@ -44,6 +44,8 @@ def run_mix(bfs, gs, handles, queries, budget=1 << 32, device_out=True, stagger=
         out = (torch.full((n,), 77, dtype=torch.int32, device="cuda") if device_out
                else torch.full((n,), 77, dtype=torch.int32).pin_memory().numpy() if k % 2 else np.full(n, 77, np.int32))
         outs.append(out)
+        if device_out:
+            torch.cuda.synchronize()  # the fill must not be pending when the server starts writing the row
         tickets.append(srv.submit(ids[gi], src, out))
         if stagger:
             time.sleep(stagger)
