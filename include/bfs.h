@@ -119,7 +119,8 @@ typedef struct bfs_params {
     int32_t ms_heavy_min;    /* bfs_multi pull levels: vertices with more entries are scanned by a
                                 whole warp (default 256) */
     int32_t ms_degree_order; /* bfs_multi pull levels visit vertices by decreasing degree (1, default)
-                                or by id (0) */
+                                or by id (0); used with ms_relabel = 0 (the renumbered copy is in
+                                degree order already) */
     int32_t ms_alpha;        /* bfs_multi: a push level is followed by a pull level when
                                 ms_alpha * (degree sum of the new frontier) > entries of vertices not
                                 yet reached by every lane (default 2: a pull level scans those lists
@@ -249,7 +250,9 @@ int bfs_single_ex(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *pa
  *  dist       [k][n] row-major (row i = distances from srcs[i]), device or host
  *             memory (detected); dist_bits 8 (uint8, 255 = unreachable) or 32
  *             (int32, -1 = unreachable).
- * Sources are processed in groups of bfs_params.ms_lanes (default 256).
+ * Sources are processed in groups of bfs_params.ms_lanes (default 256).  The
+ * first call on a graph builds its degree-renumbered copy (bfs_params.ms_relabel)
+ * and the group workspace: (2 + ms_ring) * 32 bytes per vertex for 256 lanes.
  * Blocks until done.  Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ERANGE
  * (uint8 output and a distance above 254: dist is then incomplete).
  */
