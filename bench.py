@@ -651,6 +651,70 @@ def run_serve(args):
     return 0
 
 
+def run_dup(args):
+    """The paper's non-atomic top-down variant (Section 2, BFS-NonAtomic): duplicate frontier
+    entries per level and its time per BFS, next to the atomic top-down and the hybrid
+    single-source runs on the same sources (4 sources per graph)."""
+    import torch
+
+    import graphgen
+    import paper_2503_00430_gb300 as bfs
+    torch.cuda.set_device(0)
+    specs = [("rmat_s24", lambda: graphgen.rmat(24, EDGEFACTOR, 0.57, 0.19, 0.19, 1, 1)),
+             ("er_2e22_d16", lambda: graphgen.erdos_renyi(1 << 22, 16.0, 5)),
+             ("grid_1024x1024", lambda: graphgen.grid2d(1024, 1024))]
+    e0, e1 = _events()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    for name, make in specs:
+        rp, col = make()
+        n = len(rp) - 1
+        g = bfs.bfs_graph_upload(rp, col)
+        d = torch.empty(n, dtype=torch.int32, device="cuda")
+        res = []
+        for src in graphgen.sources(rp, 4, 1007):
+            src = int(src)
+            try:
+                st, lv = bfs.bfs_single_nonatomic(g, src, d, level_cap=1 << 14)
+            except bfs.BfsError as err:  # duplicates beyond the n + m queue: a result, not a crash
+                if err.code != bfs.BFS_ENOMEM:
+                    raise
+                res.append({"src": src, "overflow": True})
+                continue
+            dup = [(x["frontier"] - x["unique"]) / x["unique"] for x in lv if x["unique"] > 0]
+            big = [(i, (x["frontier"] - x["unique"]) / x["unique"]) for i, x in enumerate(lv) if x["unique"] >= 1000]
+            worst = max(big, key=lambda t: t[1]) if big else (None, 0.0)
+            res.append({
+                "src": src, "levels": st["levels"], "reached": st["unique"],
+                "dup_fraction": (st["frontier_entries"] - st["unique"]) / st["unique"],
+                "max_level_dup_fraction": max(dup) if dup else 0.0,
+                "max_dup_level_with_1000_vertices": worst[0], "its_fraction": worst[1],
+                "ms_nonatomic": timed(lambda: bfs.bfs_single_nonatomic(g, src, d, stats=False)),
+                "ms_atomic_topdown": timed(lambda: bfs.bfs_single_ex(g, src, d, params=bfs.make_params(policy=3))),
+                "ms_hybrid": timed(lambda: bfs.bfs_single(g, src, d)),
+            })
+        ok = [r for r in res if not r.get("overflow")]
+        agg = {k: float(np.mean([r[k] for r in ok])) if ok else None
+               for k in ("dup_fraction", "max_level_dup_fraction", "ms_nonatomic", "ms_atomic_topdown", "ms_hybrid")}
+        out[name] = {"n": n, "m": int(len(col)), "overflows": len(res) - len(ok), "mean": agg, "sources": res}
+        g.free()
+        del rp, col
+    _json({"metric": "duplicate frontier entries of the non-atomic top-down BFS (fraction of distinct)",
+           "value": out["rmat_s24"]["mean"]["dup_fraction"], "unit": "fraction", "higher_is_better": False,
+           "n_gpus": 1, "dtype": "int32", "data": "synthetic", "config": {"workload": "nonatomic_duplicates", **out}})
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -667,7 +731,7 @@ def main(argv=None):
     ap.add_argument("--no-degree-order", action="store_true",
                     help="keep the generator's id-sorted adjacency order on the device")
     ap.add_argument("--workload", default="rmat25",
-                    choices=["rmat25", "er24", "large", "msbfs", "graphset", "serve"])
+                    choices=["rmat25", "er24", "large", "msbfs", "graphset", "serve", "dup"])
     ap.add_argument("--graphs", type=int, default=10000, help="graphset: graphs in the set")
     ap.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per offered rate")
     args = ap.parse_args(argv)
@@ -679,7 +743,8 @@ def main(argv=None):
         args.relabel = RELABEL_DEFAULT.get(args.workload, 0)
     if args.workload in ("rmat25", "er24"):
         return run_ours(args)
-    return {"large": run_large, "msbfs": run_msbfs, "graphset": run_graphset, "serve": run_serve}[args.workload](args)
+    return {"large": run_large, "msbfs": run_msbfs, "graphset": run_graphset, "serve": run_serve,
+            "dup": run_dup}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -181,6 +181,23 @@ typedef struct bfs_multi_stats {
     int64_t reserved[4];
 } bfs_multi_stats;
 
+/* Per-level counts of bfs_single_nonatomic (level L expands the frontier F_L). */
+typedef struct bfs_dup_level {
+    int64_t frontier;        /* entries appended when F_L was found, duplicates included */
+    int64_t unique;          /* distinct vertices among them (|F_L|) */
+    int64_t edges;           /* list entries read expanding F_L */
+} bfs_dup_level;
+
+/* Totals of bfs_single_nonatomic. */
+typedef struct bfs_dup_stats {
+    int32_t levels;          /* levels expanded (eccentricity of src + 1) */
+    int32_t pad;
+    int64_t frontier_entries;/* sum over levels of appended entries, duplicates included */
+    int64_t unique;          /* sum over levels of distinct frontier vertices (= reached vertices) */
+    int64_t edges;           /* sum over levels of list entries read */
+    int64_t reserved[4];
+} bfs_dup_stats;
+
 /* Message for a BFS_* code (static string). */
 const char *bfs_strerror(int code);
 
@@ -261,6 +278,28 @@ int bfs_multi(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist
 /* bfs_multi with parameters (NULL = defaults) and optional counters (NULL = none). */
 int bfs_multi_ex(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int dist_bits,
                  const bfs_params *params, bfs_multi_stats *stats, void *stream);
+
+/*
+ * The paper's BFS-NonAtomic top-down traversal (Section 2, Listing 1 with the
+ * byte-map visited set of Listing 3), kept to measure its duplicates: a thread
+ * that finds neighbour v unvisited marks it (visited byte, dist = L + 1) with
+ * plain stores and appends it to the next frontier without claiming it, so two
+ * threads that test v at the same time both append it.  Distances are exact
+ * (every writer of a level stores the same value).  On a GPU a level's tests
+ * run nearly at once and duplicates would multiply from level to level if they
+ * were expanded again, so before a level is expanded its entries are reduced
+ * to distinct vertices without atomics (each entry stores its index into a
+ * per-vertex slot; the entry whose index remains is kept).
+ * Top-down levels only, one launch sequence per level, blocks until done.
+ *  dist       device int32[n] (-1 = unreachable), written on `stream`.
+ *  stats      NULL or totals; levels NULL or per-level counts for the first
+ *             level_cap levels.
+ * The first call allocates its workspace (5 bytes per vertex and two queues of
+ * n + m + 1 entries, kept until bfs_graph_free).  Errors: BFS_EINVAL (also
+ * n + m + 1 >= 2^31), BFS_ENOMEM, BFS_ECUDA.
+ */
+int bfs_single_nonatomic(bfs_graph *g, int32_t src, int32_t *dist, bfs_dup_stats *stats, bfs_dup_level *levels,
+                         int32_t level_cap, void *stream);
 
 /* ---- autotuner ---- */
 

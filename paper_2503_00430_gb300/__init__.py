@@ -93,6 +93,23 @@ class bfs_multi_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class bfs_dup_level(ctypes.Structure):
+    _fields_ = [("frontier", ctypes.c_int64), ("unique", ctypes.c_int64), ("edges", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bfs_dup_stats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32), ("pad", ctypes.c_int32), ("frontier_entries", ctypes.c_int64),
+        ("unique", ctypes.c_int64), ("edges", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "pad")}
+
+
 class bfs_graphset_stats(ctypes.Structure):
     _fields_ = [
         ("graphs", ctypes.c_int32), ("max_levels", ctypes.c_int32), ("blocks", ctypes.c_int32),
@@ -152,6 +169,8 @@ _SIGNATURES = [
     ("bfs_single_ex", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_stats),
                                      _vp, _i32, _vp]),
     ("bfs_single_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _i64, _i32, _vp, _vp]),
+    ("bfs_single_nonatomic", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_dup_stats),
+                                            ctypes.POINTER(bfs_dup_level), _i32, _vp]),
     ("bfs_multi", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, _vp]),
     ("bfs_multi_ex", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.POINTER(bfs_params),
                                     ctypes.POINTER(bfs_multi_stats), _vp]),
@@ -357,6 +376,18 @@ def bfs_multi_ex(g: Graph, srcs, dist, dist_bits: int = 32, params: bfs_params |
                                ctypes.byref(params) if params is not None else None, ctypes.byref(st),
                                _stream_handle(stream)), "bfs_multi_ex")
     return st.as_dict()
+
+
+def bfs_single_nonatomic(g: Graph, src: int, dist, level_cap: int = 0, stats: bool = True, stream=None):
+    """The paper's non-atomic top-down BFS (duplicates allowed); returns (totals or None, per-level list)."""
+    st = bfs_dup_stats() if stats else None
+    lv = (bfs_dup_level * level_cap)() if level_cap > 0 else None
+    _check(load().bfs_single_nonatomic(g.handle, int(src), _ptr(dist), ctypes.byref(st) if st is not None else None,
+                                       lv, level_cap, _stream_handle(stream)), "bfs_single_nonatomic")
+    levels = [] if lv is None else [x.as_dict() for x in lv]
+    if st is not None:
+        levels = levels[:st.levels]
+    return (st.as_dict() if st is not None else None), levels
 
 
 class GraphSet:

@@ -161,6 +161,8 @@ void release_graph(bfs_graph* g) {
   free_single_ws(g);
   free_multi_ws(g);
   free_relabel(g);
+  free_nonatomic_ws(g->na);
+  g->na = nullptr;
   if (g->rp) cudaFree(g->rp);
   if (g->col) cudaFree(g->col);
   if (g->init_vis) cudaFree(g->init_vis);
@@ -462,6 +464,16 @@ int bfs_multi_ex(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int d
   if (stats) memset(stats, 0, sizeof(*stats));
   std::lock_guard<std::mutex> lock(g->mu);
   return run_multi(g, srcs, k, dist, dist_bits, p, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int bfs_single_nonatomic(bfs_graph* g, int32_t src, int32_t* dist, bfs_dup_stats* stats, bfs_dup_level* levels,
+                         int32_t level_cap, void* stream) {
+  if (!g || !dist) return BFS_EINVAL;
+  if (src < 0 || (int64_t)src >= g->n) return BFS_EINVAL;
+  if (level_cap < 0 || (level_cap > 0 && !levels)) return BFS_EINVAL;
+  if (!is_device_pointer(dist)) return BFS_EINVAL;
+  std::lock_guard<std::mutex> lock(g->mu);
+  return run_nonatomic(g, src, dist, stats, levels, level_cap, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int bfs_multi(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int dist_bits, void* stream) {

@@ -139,6 +139,7 @@ struct SingleWs {
 
 namespace gbfs {
 struct MultiWs;
+struct NonAtomicWs;
 
 // A copy of the graph with the vertices renumbered by decreasing degree (ties
 // by id): new id i is the i-th vertex of that order.  Multi-source levels run
@@ -175,6 +176,7 @@ struct bfs_graph {
   gbfs::SingleWs ws;
   gbfs::MultiWs* ms = nullptr;  // multi-source workspace (bfs_multi.cu)
   gbfs::Relabel* rl = nullptr;  // degree-renumbered copy (bfs_reorder.cu), built on first use
+  gbfs::NonAtomicWs* na = nullptr;  // bfs_single_nonatomic workspace (bfs_nonatomic.cu)
   bool deg_ordered = false;     // lists were sorted highest degree first at upload
 };
 
@@ -198,6 +200,9 @@ int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
                bfs_level_stat* levels, int level_cap, cudaStream_t stream);
+int run_nonatomic(bfs_graph* g, int src, int* dist, bfs_dup_stats* st, bfs_dup_level* lv, int lv_cap,
+                  cudaStream_t s);
+void free_nonatomic_ws(NonAtomicWs* ws);
 int ensure_multi_ws(bfs_graph* g, int ring);
 void free_multi_ws(bfs_graph* g);
 int run_multi(bfs_graph* g, const int32_t* srcs, int k, void* dist, int bits, const bfs_params& p,
