@@ -280,6 +280,18 @@ int bfs_multi_ex(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int d
                  const bfs_params *params, bfs_multi_stats *stats, void *stream);
 
 /*
+ * A BFS tree from finished distances (Graph500-style parent array; the paper
+ * computes distances only).  dist: device int32[n] from a query on g (any
+ * entry point); parent: device int32[n], written on `stream`: the parent of a
+ * reached vertex v other than the source is the first vertex u of v's list (in
+ * the library's list order, see BFS_DEGREE_ORDER) with dist[u] = dist[v] - 1;
+ * the vertex at distance 0 is its own parent; unreached vertices get -1.
+ * A reached vertex with no such neighbour (dist not a BFS result of g) gets -1.
+ * Asynchronous.  Errors: BFS_EINVAL (null or host pointers), BFS_ECUDA.
+ */
+int bfs_parents(bfs_graph *g, const int32_t *dist, int32_t *parent, void *stream);
+
+/*
  * The paper's BFS-NonAtomic top-down traversal (Section 2, Listing 1 with the
  * byte-map visited set of Listing 3), kept to measure its duplicates: a thread
  * that finds neighbour v unvisited marks it (visited byte, dist = L + 1) with

@@ -169,6 +169,7 @@ _SIGNATURES = [
     ("bfs_single_ex", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_stats),
                                      _vp, _i32, _vp]),
     ("bfs_single_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _i64, _i32, _vp, _vp]),
+    ("bfs_parents", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("bfs_single_nonatomic", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_dup_stats),
                                             ctypes.POINTER(bfs_dup_level), _i32, _vp]),
     ("bfs_multi", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, _vp]),
@@ -376,6 +377,11 @@ def bfs_multi_ex(g: Graph, srcs, dist, dist_bits: int = 32, params: bfs_params |
                                ctypes.byref(params) if params is not None else None, ctypes.byref(st),
                                _stream_handle(stream)), "bfs_multi_ex")
     return st.as_dict()
+
+
+def bfs_parents(g: Graph, dist, parent, stream=None) -> None:
+    """Parent array (BFS tree) of finished distances: first list neighbour one level closer."""
+    _check(load().bfs_parents(g.handle, _ptr(dist), _ptr(parent), _stream_handle(stream)), "bfs_parents")
 
 
 def bfs_single_nonatomic(g: Graph, src: int, dist, level_cap: int = 0, stats: bool = True, stream=None):

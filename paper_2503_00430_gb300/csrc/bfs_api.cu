@@ -466,6 +466,12 @@ int bfs_multi_ex(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int d
   return run_multi(g, srcs, k, dist, dist_bits, p, stats, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int bfs_parents(bfs_graph* g, const int32_t* dist, int32_t* parent, void* stream) {
+  if (!g || !dist || !parent) return BFS_EINVAL;
+  if (!is_device_pointer(dist) || !is_device_pointer(parent)) return BFS_EINVAL;
+  return run_parents(g, dist, parent, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int bfs_single_nonatomic(bfs_graph* g, int32_t src, int32_t* dist, bfs_dup_stats* stats, bfs_dup_level* levels,
                          int32_t level_cap, void* stream) {
   if (!g || !dist) return BFS_EINVAL;
