@@ -11,6 +11,10 @@
 
 namespace gbfs {
 
+// Parent arrays (bfs_parents.cu).
+int run_parents(bfs_graph* g, const int* dist, int* parent, cudaStream_t s);
+void free_parent_ws_of(const bfs_graph* g);
+
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
   fprintf(stderr, "libbfs: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) {
@@ -163,6 +167,7 @@ void release_graph(bfs_graph* g) {
   free_relabel(g);
   free_nonatomic_ws(g->na);
   g->na = nullptr;
+  free_parent_ws_of(g);
   if (g->rp) cudaFree(g->rp);
   if (g->col) cudaFree(g->col);
   if (g->init_vis) cudaFree(g->init_vis);
@@ -469,6 +474,7 @@ int bfs_multi_ex(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int d
 int bfs_parents(bfs_graph* g, const int32_t* dist, int32_t* parent, void* stream) {
   if (!g || !dist || !parent) return BFS_EINVAL;
   if (!is_device_pointer(dist) || !is_device_pointer(parent)) return BFS_EINVAL;
+  std::lock_guard<std::mutex> lock(g->mu);
   return run_parents(g, dist, parent, reinterpret_cast<cudaStream_t>(stream));
 }
 

@@ -69,12 +69,15 @@ def run(B, g, n, src, **kw):
 @pytest.mark.parametrize("bits", [32, 64])
 def test_first_rule_and_invariants(bfs, bits):
     # A vertex (1) whose parent (200) is entry 100 of its list: the warp-cooperative scan.
+    # A star searched from a far leaf: the centre's parent is entry ~2500 of a 2999-entry list, past the
+    # warp-scanned part: the chunked scan of long lists.
     edges = [(0, 200), (200, 1)] + [(1, 2 + i) for i in range(100)] + [(300, 301)]
-    cases = [graphgen.rmat(14, seed=51), graphgen.grid2d(20, 30), G.csr_from_edges(310, edges), G.star_graph(600)]
-    for rp, col in cases:
+    cases = [(graphgen.rmat(14, seed=51), []), (graphgen.grid2d(20, 30), []), (G.csr_from_edges(310, edges), []),
+             (G.star_graph(600), []), (G.star_graph(3000), [2500, 40])]
+    for (rp, col), extra in cases:
         g = bfs.bfs_graph_upload(rp.astype(np.int32 if bits == 32 else np.int64), col)
         n = len(rp) - 1
-        for src in list(graphgen.sources(rp, 2, 5100)) + [0]:
+        for src in list(graphgen.sources(rp, 2, 5100)) + [0] + extra:
             want = oracle.bfs(rp, col, int(src))
             d, par = run(bfs, g, n, src)
             assert np.array_equal(d, want)
