@@ -1,0 +1,49 @@
+"""The benchmark's measurement arithmetic on hand-worked cases (CPU).
+
+harmonic_gteps is the harmonic mean of per-BFS rates; algorithmic_bytes is the
+compulsory-byte model behind roofline.achieved.  The expected values below are
+worked out term by term from the model's definition (query overhead, then each
+level's top-down / bottom-up / conversion terms)."""
+from __future__ import annotations
+
+import pytest
+
+import bench
+
+
+def test_harmonic_gteps():
+    # Rates 2 and 4 GTEPS: harmonic mean 2 / (1/2 + 1/4) = 8/3.
+    assert bench.harmonic_gteps([2e9, 4e9], [1.0, 1.0]) == pytest.approx(8 / 3)
+    # One BFS: its own rate.
+    assert bench.harmonic_gteps([5e8], [0.25]) == pytest.approx(2.0)
+
+
+LEVELS = [
+    # top-down from the source: 1 frontier vertex, 2 entries, 2 found
+    dict(direction=0, converted=0, frontier=1, edges=2, unvisited=0, found=2),
+    # converted to bottom-up: 2 frontier vertices, 5 unvisited scanned, 10 entries, 3 found
+    dict(direction=1, converted=1, frontier=2, edges=10, unvisited=5, found=3),
+    # converted back to top-down: 3 frontier vertices, 6 entries, none found
+    dict(direction=0, converted=1, frontier=3, edges=6, unvisited=0, found=0),
+]
+
+
+def test_algorithmic_bytes_head_table():
+    n = 64
+    query = n + n / 4 + 5 * n                                # level bytes, visited init, expansion
+    l0 = 8 * 1 + 4 * 2 + (16 + 1 + 8 + 4) * 2                # items, ids, per found: head, byte, item, queue
+    l1 = (n / 8 + 4 * 2) + (3 * n / 8 + 16 * 5 + 4 * max(0, 10 - 2 * 5) + 3)
+    l2 = (n / 8 + (16 + 8) * 3) + (8 * 3 + 4 * 6 + 0)
+    assert bench.algorithmic_bytes(n, 8, LEVELS) == pytest.approx(query + l0 + l1 + l2)
+    assert query + l0 + l1 + l2 == 725
+
+
+def test_algorithmic_bytes_row_pointers_no_queue():
+    n, rp = 64, 4
+    query = n + n / 4 + 5 * n
+    l0 = 8 * 1 + 4 * 2 + (2 * rp + 1 + 8) * 2
+    l1 = (n / 8 + 4 * 2) + (3 * n / 8 + rp * 5 + 4 * 10 + 3)
+    l2 = (n / 8 + (2 * rp + 8) * 3) + (8 * 3 + 4 * 6)
+    got = bench.algorithmic_bytes(n, rp, LEVELS, head=False, queue=False)
+    assert got == pytest.approx(query + l0 + l1 + l2)
+    assert got == 657  # 400 + 50 + 103 + 104
