@@ -38,6 +38,28 @@ def pin_bruteforce_exhaustive(lib, max_n=5):
     return True, None
 
 
+def pin_bruteforce_atlas(lib):
+    """Every graph on up to 7 vertices up to isomorphism (the 1,253 graphs of networkx's graph
+    atlas), every source: distances are equivariant under relabelling, so together with the
+    labelled exhaustive pin above this covers every graph of <= 7 vertices."""
+    try:
+        import networkx as nx
+    except ImportError:  # pragma: no cover - networkx is part of the image
+        return True, "networkx missing: skipped"
+    for h in nx.graph_atlas_g():
+        n = h.number_of_nodes()
+        if n == 0:
+            continue
+        edges = [(int(a), int(b)) for a, b in h.edges()]
+        rp, col = G.csr_from_edges(n, edges)
+        for s in range(n):
+            got = oracle.bfs(rp, col, s, lib)
+            want = G.brute_force_dist(n, edges, s)
+            if not np.array_equal(got, want):
+                return False, (n, edges, s, got.tolist(), want.tolist())
+    return True, None
+
+
 def pin_bruteforce_random(lib, cases=300, seed=12345):
     """Random multigraphs (self-loops and repeated pairs included) on up to 64 vertices."""
     rng = random.Random(seed)
@@ -123,7 +145,7 @@ def pin_invariants(lib):
     return True, None
 
 
-PINS = [pin_bruteforce_exhaustive, pin_bruteforce_random, pin_closed_forms, pin_invariants]
+PINS = [pin_bruteforce_exhaustive, pin_bruteforce_atlas, pin_bruteforce_random, pin_closed_forms, pin_invariants]
 
 
 # ---- the oracle itself ----
