@@ -94,6 +94,45 @@ def make_workload(args):
     return rp, col, srcs, 8, f"rmat_s{args.scale}_ef16_hybrid_64src"
 
 
+def upload_flags(bfs, args):
+    """bfs_graph_upload flags of the single-source workloads (degree-ordered lists unless disabled)."""
+    return bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER)
+
+
+def query_params(bfs, args):
+    """bfs_params of the timed single-source queries."""
+    return bfs.make_params(policy=args.policy, launch=args.launch, relabel=args.relabel)
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=SCALE)
+    ap.add_argument("--policy", type=int, default=0)
+    ap.add_argument("--launch", type=int, default=0)
+    ap.add_argument("--relabel", type=int, default=None, choices=[0, 1],
+                    help="single-source queries on the degree-renumbered copy of the graph")
+    ap.add_argument("--cpu-sample", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-degree-order", action="store_true",
+                    help="keep the generator's id-sorted adjacency order on the device")
+    ap.add_argument("--workload", default="rmat25",
+                    choices=["rmat25", "er24", "large", "msbfs", "graphset", "serve", "dup"])
+    ap.add_argument("--graphs", type=int, default=10000, help="graphset: graphs in the set")
+    ap.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per offered rate")
+    ap.add_argument("--no-msbfs", action="store_true",
+                    help="rmat25: skip the multi-source line added to the single-source result")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.relabel is None:
+        args.relabel = RELABEL_DEFAULT.get(args.workload, 0)
+    return args
+
+
 def aggregate_ranks(total_ms, value, device="cuda"):
     """Max of the timed region over ranks and the sum of the per-rank rates
     (independent replicas: the job's throughput is the sum)."""
@@ -119,10 +158,40 @@ def harmonic_gteps(edges, seconds):
     return float(len(edges) / np.sum(seconds / edges) / 1e9)
 
 
-def algorithmic_bytes(n, rp_bytes, levels, head=True, queue=True):
-    """Compulsory DRAM bytes of one BFS from its per-level counters, for the
-    library's layout: per-vertex level bytes while the search runs, expanded
-    to int32 distances at the end, and (``head``) the 16-byte head table.
+def algorithmic_bytes(n, rp_bytes, levels, l2_bytes=L2_BYTES):
+    """Compulsory DRAM bytes of one BFS from its per-level counters: the bytes
+    the method itself must move at word granularity, independent of this
+    library's layout (per BFS, RP = bytes of a row pointer):
+
+    query init: 4n (dist) + n/8 (visited);
+    top-down level L: 4|F_L| (queue read) + 2*RP*|F_L| (row-pointer pair)
+    + 4*E_td (neighbour ids) + 4|F_L+1| (dist store) + 4|F_L+1| (queue append);
+    bottom-up level L: 3n/8 (visited read, next-frontier write, visited update)
+    + RP*U_L (row pointer of each unvisited vertex of degree > 0)
+    + 4*E_bu (entries examined up to and including the first frontier
+    neighbour, all of them on a miss) + 4|F_L+1| (dist);
+    each queue <-> bitmap conversion: n/8 + 4|F|.
+    Random visited / frontier bit probes are not counted while a bitmap fits in
+    half of L2 (n/8 <= L2/2); above that each probe costs 4 bytes (one per
+    top-down neighbour, one per bottom-up entry examined)."""
+    probe = 4 if n / 8 > l2_bytes / 2 else 0
+    b = 4 * n + n / 8
+    for lv in levels:
+        f, e, u, fn = lv["frontier"], lv["edges"], lv["unvisited"], lv["found"]
+        if lv["converted"]:
+            b += n / 8 + 4 * f
+        if lv["direction"] == 0:
+            b += 4 * f + 2 * rp_bytes * f + (4 + probe) * e + 8 * fn
+        else:
+            b += 3 * n / 8 + rp_bytes * u + (4 + probe) * e + 4 * fn
+    return b
+
+
+def layout_bytes(n, rp_bytes, levels, head=True, queue=True):
+    """DRAM bytes of one BFS for this library's own layout (reported beside
+    the compulsory bytes, not used for the roofline): per-vertex level bytes
+    while the search runs, expanded to int32 distances at the end, and
+    (``head``) the 16-byte head table.
 
     query: level bytes n + visited init n/8 (read mask) + n/8 (write), final
     expansion n (read) + 4n (write);
@@ -207,6 +276,24 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_info():
+    """The host the CPU baseline runs on: logical CPUs (nproc) and lscpu's model name."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    try:
+        nproc = int(subprocess.run(["nproc"], capture_output=True, text=True, timeout=10).stdout.strip())
+    except Exception:
+        nproc = os.cpu_count()
+    return {"nproc": nproc, "cpu_model": model, "machine": os.uname().machine}
+
+
 def cpu_baseline(rp, col, srcs, nsample):
     if nsample <= 0:
         return None
@@ -220,8 +307,8 @@ def cpu_baseline(rp, col, srcs, nsample):
         secs.append(time.perf_counter() - t0)
         edges.append(float(deg[d >= 0].sum()) / 2)
     return {"value": harmonic_gteps(edges, secs), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"{nsample} of the {len(srcs)} sources on the same s{SCALE} graph, serial queue BFS",
-            "seconds": float(sum(secs))}
+            "sample": f"{nsample} of the {len(srcs)} sources on the same graph, serial queue BFS",
+            "seconds": float(sum(secs)), "host": host_info()}
 
 
 def run_reference(args):
@@ -248,7 +335,8 @@ def run_reference(args):
                       "edgefactor": EDGEFACTOR, "n": int(len(rp) - 1), "m": int(len(col)),
                       "step": "one serial oracle BFS from the next of the 64 sources"},
            "cpu_baseline": {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                            "sample": f"{args.steps} timed sources (1 per step) of the same graph"},
+                            "sample": f"{args.steps} timed sources (1 per step) of the same graph",
+                            "host": host_info()},
            "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -272,8 +360,8 @@ def run_ours(args):
     srcs = np.asarray(replica_sources(srcs, rank, world), dtype=np.int32)
     t_gen = time.perf_counter() - t_gen
     n, m = len(rp) - 1, len(col)
-    g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER))
-    params = bfs.make_params(policy=args.policy, launch=args.launch, relabel=args.relabel)
+    g = bfs.bfs_graph_upload(rp, col, flags=upload_flags(bfs, args))
+    params = query_params(bfs, args)
     has_head = m < (1 << 31) - 8  # the library builds the head table when list starts fit int32
     hybrid = not (args.policy == bfs.BFS_POLICY_TD_ONLY or (args.policy == bfs.BFS_POLICY_AUTO and m < 7 * n))
     stream = torch.cuda.Stream()
@@ -283,8 +371,8 @@ def run_ours(args):
     per_src = []
     for s in srcs:
         st, lv = bfs.bfs_single_ex(g, int(s), dist_buf, params=params, stats=True, level_cap=1 << 16, stream=stream)
-        per_src.append({"edges": st["edges_reached"] / 2, "stats": st,
-                        "bytes": algorithmic_bytes(n, rp_bytes, lv, head=has_head, queue=hybrid)})
+        per_src.append({"edges": st["edges_reached"] / 2, "stats": st, "bytes": algorithmic_bytes(n, rp_bytes, lv),
+                        "layout_bytes": layout_bytes(n, rp_bytes, lv, head=has_head, queue=hybrid)})
 
     def one_step(times):
         for i, s in enumerate(srcs):
@@ -374,7 +462,12 @@ def run_ours(args):
                      "traffic": traffic,
                      "traffic_vs_algorithmic": traffic_ratio,
                      "kernel": "bfs_persistent_kernel<long long,false> (one launch per BFS)",
-                     "bytes_per_bfs_mean": float(np.mean([p["bytes"] for p in per_src]))},
+                     "bytes_per_bfs_mean": float(np.mean([p["bytes"] for p in per_src])),
+                     "bytes_model": "compulsory bytes of the method (init 4n+n/8; top-down 4F+2RP*F+4E+8F'; "
+                                    "bottom-up 3n/8+RP*U+4E+4F'; conversion n/8+4F)",
+                     "layout_bytes_per_bfs_mean": float(np.mean([p["layout_bytes"] for p in per_src])),
+                     "layout_frac": float(np.sum([per_src[i]["layout_bytes"] for i, _, _ in recs]) / np.sum(secs)
+                                          / 1e9 / hbm)},
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": len(recs),
@@ -403,6 +496,34 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+LARGE_SRC_SEED = 1003
+MSBFS_SRC_SEED = 1004
+SERVE_SRC_SEED = 1005
+
+
+def large_specs():
+    """(name, generator) of the large-diameter workloads: 2-D grid 4096^2 and a
+    random geometric graph of 2^23 points at mean degree 3."""
+    import graphgen
+    return [("grid_4096x4096", lambda: graphgen.grid2d(4096, 4096)),
+            ("rgg_2e23_d3", lambda: graphgen.rgg(1 << 23, graphgen.rgg_radius(1 << 23, 3.0), 3))]
+
+
+def msbfs_workload():
+    """R-MAT scale 24 (edge factor 16, ids permuted with seed 1) and its 256 sources."""
+    import graphgen
+    rp, col = graphgen.rmat(24, EDGEFACTOR, 0.57, 0.19, 0.19, 1, 1)
+    return rp, col, graphgen.sources(rp, 256, MSBFS_SRC_SEED)
+
+
+def serve_specs():
+    """(name, generator) of the five resident graphs of the serving workload."""
+    import graphgen
+    return [("rmat_s20", lambda: graphgen.rmat(20)), ("rmat_s22", lambda: graphgen.rmat(22)),
+            ("rmat_s24", lambda: graphgen.rmat(24)), ("grid_2048x2048", lambda: graphgen.grid2d(2048, 2048)),
+            ("er_2e22_d16", lambda: graphgen.erdos_renyi(1 << 22, 16.0, 5))]
+
+
 def run_large(args):
     """Large-diameter graphs: 2-D grid 4096^2 and a random geometric graph of 2^23 points.
 
@@ -417,10 +538,9 @@ def run_large(args):
     import paper_2503_00430_gb300 as bfs
     torch.cuda.set_device(0)
     res = {}
-    for name, make in (("grid_4096x4096", lambda: graphgen.grid2d(4096, 4096)),
-                       ("rgg_2e23_d3", lambda: graphgen.rgg(1 << 23, graphgen.rgg_radius(1 << 23, 3.0), 3))):
+    for name, make in large_specs():
         rp, col = make()
-        srcs = graphgen.sources(rp, 8, 1003)
+        srcs = graphgen.sources(rp, 8, LARGE_SRC_SEED)
         g = bfs.bfs_graph_upload(rp.astype(np.int32), col, flags=bfs.BFS_VALIDATE)
         n = len(rp) - 1
         d = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -462,9 +582,8 @@ def run_msbfs(args):
     import graphgen
     import paper_2503_00430_gb300 as bfs
     torch.cuda.set_device(0)
-    rp, col = graphgen.rmat(24, EDGEFACTOR, 0.57, 0.19, 0.19, 1, 1)
+    rp, col, srcs = msbfs_workload()
     n = len(rp) - 1
-    srcs = graphgen.sources(rp, 256, 1004)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | bfs.BFS_DEGREE_ORDER)
     d = torch.empty(n, dtype=torch.int32, device="cuda")
     for s_ in srcs[:4]:
@@ -555,15 +674,12 @@ def run_serve(args):
     import graphgen
     import paper_2503_00430_gb300 as bfs
     torch.cuda.set_device(0)
-    specs = [("rmat_s20", lambda: graphgen.rmat(20)), ("rmat_s22", lambda: graphgen.rmat(22)),
-             ("rmat_s24", lambda: graphgen.rmat(24)), ("grid_2048x2048", lambda: graphgen.grid2d(2048, 2048)),
-             ("er_2e22_d16", lambda: graphgen.erdos_renyi(1 << 22, 16.0, 5))]
     graphs, handles, srcpool = [], [], []
-    for name, make in specs:
+    for name, make in serve_specs():
         rp, col = make()
         graphs.append((name, len(rp) - 1))
         handles.append(bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_DEGREE_ORDER))
-        srcpool.append(graphgen.sources(rp, 4096, 1005))
+        srcpool.append(graphgen.sources(rp, 4096, SERVE_SRC_SEED))
         del rp, col
     rng = np.random.default_rng(5)
 
@@ -716,31 +832,9 @@ def run_dup(args):
 
 
 def main(argv=None):
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--scale", type=int, default=SCALE)
-    ap.add_argument("--policy", type=int, default=0)
-    ap.add_argument("--launch", type=int, default=0)
-    ap.add_argument("--relabel", type=int, default=None, choices=[0, 1],
-                    help="single-source queries on the degree-renumbered copy of the graph")
-    ap.add_argument("--cpu-sample", type=int, default=2)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-degree-order", action="store_true",
-                    help="keep the generator's id-sorted adjacency order on the device")
-    ap.add_argument("--workload", default="rmat25",
-                    choices=["rmat25", "er24", "large", "msbfs", "graphset", "serve", "dup"])
-    ap.add_argument("--graphs", type=int, default=10000, help="graphset: graphs in the set")
-    ap.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per offered rate")
-    args = ap.parse_args(argv)
-    if args.warmup < 3:
-        args.warmup = 3
+    args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
-    if args.relabel is None:
-        args.relabel = RELABEL_DEFAULT.get(args.workload, 0)
     if args.workload in ("rmat25", "er24"):
         return run_ours(args)
     return {"large": run_large, "msbfs": run_msbfs, "graphset": run_graphset, "serve": run_serve,

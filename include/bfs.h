@@ -287,7 +287,11 @@ int bfs_multi_ex(bfs_graph *g, const int32_t *srcs, int32_t k, void *dist, int d
  * the library's list order, see BFS_DEGREE_ORDER) with dist[u] = dist[v] - 1;
  * the vertex at distance 0 is its own parent; unreached vertices get -1.
  * A reached vertex with no such neighbour (dist not a BFS result of g) gets -1.
- * Asynchronous.  Errors: BFS_EINVAL (null or host pointers), BFS_ECUDA.
+ * Asynchronous.  Calls on one graph share a small device workspace; the
+ * library orders them on the device (each call waits for the previous one's
+ * completion, whatever stream either used), so calls from several streams or
+ * threads are safe but do not overlap.  Errors: BFS_EINVAL (null or host
+ * pointers), BFS_ECUDA.
  */
 int bfs_parents(bfs_graph *g, const int32_t *dist, int32_t *parent, void *stream);
 
@@ -461,7 +465,13 @@ void bfs_serve_destroy(bfs_server *srv);
  * cudaFree, no allocating library routine.
  *  row_ptr, row_ptr_bits, col_idx, n, m   the CSR graph as in
  *        bfs_graph_upload, but already in DEVICE memory and not copied or
- *        validated (it must be a valid symmetric CSR).
+ *        validated (it must be a valid symmetric CSR).  col_idx must start on
+ *        a 16-byte boundary (the kernel reads it with aligned 16-byte loads,
+ *        which may touch up to 3 entries past m inside the 16-byte block that
+ *        holds the last entry; that block must be readable device memory, as
+ *        it is for any cudaMalloc or caching-allocator buffer); row_ptr must
+ *        be aligned to its width and dist to 4 bytes.  A misaligned pointer
+ *        returns BFS_EINVAL before anything is launched.
  *  src   source vertex in [0, n).
  *  dist  device int32[n] output (-1 = unreachable).
  * Limit: the scratch needs about 24.5*n + m/15 bytes (each of its eleven

@@ -103,7 +103,8 @@ __host__ __device__ inline bool next_is_top_down(int policy, int alpha, int beta
       return ((script >> b) & 1ull) == 0;
     }
     case BFS_POLICY_FRONTIER:
-      // Listing 2: is_top_down = cfsz < 0.05 * N, as the exact integer test tau_inv*|F| < n.
+      // Section 2's frontier-size rule (Listing 2: top-down while |F| is below 5 % of n), taken
+      // as the exact integer test tau_inv*|F| < n.
       return (long long)tau_inv * nf_next < n;
     case BFS_POLICY_EDGES:
     default:

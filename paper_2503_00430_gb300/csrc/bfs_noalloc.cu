@@ -110,6 +110,14 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   if (n < 1 || n >= ((int64_t)1 << 31) || m < 0 || (row_ptr_bits == 32 && m >= ((int64_t)1 << 31)))
     return BFS_EINVAL;
   if (src < 0 || (int64_t)src >= n) return BFS_EINVAL;
+  // The kernel reads neighbour ids with aligned 16-byte loads, row pointers and
+  // distances with naturally aligned loads and stores: a misaligned view (an
+  // offset slice, a pool sub-allocation) would fault on the device, so it is
+  // rejected here, before anything is launched.
+  if ((m > 0 && (reinterpret_cast<uintptr_t>(col_idx) & 15u) != 0) ||
+      (reinterpret_cast<uintptr_t>(row_ptr) & (uintptr_t)(row_ptr_bits / 8 - 1)) != 0 ||
+      (reinterpret_cast<uintptr_t>(dist) & 3u) != 0)
+    return BFS_EINVAL;
   const Layout lay = layout_for(n, m);
   if (lay.total > kNoallocScratchBytes) return BFS_ENOMEM;  // graph too large for the static scratch
   int dev = 0;

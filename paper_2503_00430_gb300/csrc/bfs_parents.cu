@@ -165,17 +165,28 @@ __global__ void k_parents_finish(const int* col, int* parent, ParentWs W) {
 
 namespace {
 
-void free_ws(ParentWs* w) {
+// Host side of a graph's parent workspace.  Every call on the graph uses the
+// same device buffers, so calls are ordered on the device: each one waits for
+// the previous call's completion event before it touches the buffers, and
+// records its own (calls from different streams then run one after another).
+struct ParentHost {
+  ParentWs W;
+  cudaEvent_t done = nullptr;
+  std::mutex mu;  // makes wait-on-previous + enqueue + record one step per call
+};
+
+void free_ws(ParentHost* w) {
   if (!w) return;
-  cudaFree(w->rec);
-  cudaFree(w->best);
-  cudaFree(w->ctr);
+  cudaFree(w->W.rec);
+  cudaFree(w->W.best);
+  cudaFree(w->W.ctr);
+  if (w->done) cudaEventDestroy(w->done);
   delete w;
 }
 
 // Workspace per graph, created on the graph's first parent array.
 std::mutex g_par_mu;
-std::unordered_map<const bfs_graph*, ParentWs*> g_par;
+std::unordered_map<const bfs_graph*, ParentHost*> g_par;
 
 }  // namespace
 
@@ -189,28 +200,31 @@ void free_parent_ws_of(const bfs_graph* g) {
 }
 
 int run_parents(bfs_graph* g, const int* dist, int* parent, cudaStream_t s) {
-  ParentWs* ws = nullptr;
+  ParentHost* ws = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_par_mu);
     auto it = g_par.find(g);
     if (it != g_par.end()) ws = it->second;
-  }
-  if (!ws) {
-    ParentWs* w = new ParentWs();
-    w->cap = g->m / (kParLong + kParLane) + 2;
-    cudaError_t e = cudaMalloc(&w->rec, 3 * sizeof(unsigned long long) * (size_t)w->cap);
-    if (e == cudaSuccess) e = cudaMalloc(&w->best, sizeof(int) * (size_t)w->cap);
-    if (e == cudaSuccess) e = cudaMalloc(&w->ctr, sizeof(unsigned long long));
-    if (e != cudaSuccess) {
-      free_ws(w);
-      return cuda_fail(e, "parent workspace", __FILE__, __LINE__);
+    if (!ws) {
+      ParentHost* w = new ParentHost();
+      w->W.cap = g->m / (kParLong + kParLane) + 2;
+      cudaError_t e = cudaMalloc(&w->W.rec, 3 * sizeof(unsigned long long) * (size_t)w->W.cap);
+      if (e == cudaSuccess) e = cudaMalloc(&w->W.best, sizeof(int) * (size_t)w->W.cap);
+      if (e == cudaSuccess) e = cudaMalloc(&w->W.ctr, sizeof(unsigned long long));
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        free_ws(w);
+        return cuda_fail(e, "parent workspace", __FILE__, __LINE__);
+      }
+      g_par[g] = w;
+      ws = w;
     }
-    std::lock_guard<std::mutex> lock(g_par_mu);
-    g_par[g] = w;
-    ws = w;
   }
-  const ParentWs W = *ws;
+  std::lock_guard<std::mutex> order(ws->mu);
+  const ParentWs W = ws->W;
   const int grid = g->num_sms * 8, block = 256;
+  // The previous call on this graph (any stream) must be done with W first.
+  GBFS_CUDA(cudaStreamWaitEvent(s, ws->done, 0));
   GBFS_CUDA(cudaMemsetAsync(W.ctr, 0, sizeof(unsigned long long), s));
   if (g->rp_bits == 32) {
     k_parents<int><<<grid, block, 0, s>>>(g->rp, g->col, dist, g->n, parent, W);
@@ -221,6 +235,7 @@ int run_parents(bfs_graph* g, const int* dist, int* parent, cudaStream_t s) {
   }
   k_parents_finish<<<g->num_sms, 256, 0, s>>>(g->col, parent, W);
   GBFS_CUDA(cudaGetLastError());
+  GBFS_CUDA(cudaEventRecord(ws->done, s));
   return BFS_OK;
 }
 

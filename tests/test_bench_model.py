@@ -1,9 +1,12 @@
 """The benchmark's measurement arithmetic on hand-worked cases (CPU).
 
 harmonic_gteps is the harmonic mean of per-BFS rates; algorithmic_bytes is the
-compulsory-byte model behind roofline.achieved.  The expected values below are
-worked out term by term from the model's definition (query overhead, then each
-level's top-down / bottom-up / conversion terms)."""
+compulsory-byte model of the method behind roofline.achieved (init 4n + n/8;
+top-down 4|F| + 2*RP*|F| + 4*E_td + 4|F'| + 4|F'|; bottom-up 3n/8 + RP*U +
+4*E_bu + 4|F'|; conversion n/8 + 4|F|); layout_bytes is the library-layout
+model reported beside it.  The expected values below are worked out term by
+term from each model's definition (query overhead, then each level's
+top-down / bottom-up / conversion terms)."""
 from __future__ import annotations
 
 import pytest
@@ -28,22 +31,51 @@ LEVELS = [
 ]
 
 
-def test_algorithmic_bytes_head_table():
+def test_algorithmic_bytes_compulsory_model():
+    n = 64
+    init = 4 * n + n / 8                                     # dist, visited
+    l0 = 4 * 1 + 2 * 8 * 1 + 4 * 2 + 4 * 2 + 4 * 2          # queue, row ptrs, ids, dist, append
+    l1 = (n / 8 + 4 * 2) + (3 * n / 8 + 8 * 5 + 4 * 10 + 4 * 3)
+    l2 = (n / 8 + 4 * 3) + (4 * 3 + 2 * 8 * 3 + 4 * 6 + 0)
+    assert bench.algorithmic_bytes(n, 8, LEVELS) == pytest.approx(init + l0 + l1 + l2)
+    assert init + l0 + l1 + l2 == 544                       # 264 + 44 + 132 + 104
+    assert bench.algorithmic_bytes(n, 4, LEVELS) == pytest.approx(492)  # 264 + 36 + 112 + 80
+
+
+def test_algorithmic_bytes_counts_probes_when_bitmap_exceeds_half_l2():
+    # n/8 = 8 bytes against half of an 8-byte "L2": each of the 2 + 10 + 6 probes costs 4 bytes.
+    assert bench.algorithmic_bytes(64, 8, LEVELS, l2_bytes=8) == pytest.approx(544 + 4 * 18)
+
+
+def test_algorithmic_bytes_path_closed_form():
+    """Top-down BFS along a path of 10 vertices from one end: every level has
+    one frontier vertex and finds one (the last finds none); degrees 1, 2 x 8, 1."""
+    import oracle
+    from tests import graphs as G
+    from tests.replay import replay
+    rp, col = G.path_graph(10)
+    _, lv = replay(rp, col, 0, oracle.bfs(rp, col, 0), policy=3)
+    want = (4 * 10 + 10 / 8) + 10 * (4 + 2 * 8) + 4 * 18 + 8 * 9
+    assert bench.algorithmic_bytes(10, 8, lv) == pytest.approx(want)
+    assert want == 385.25
+
+
+def test_layout_bytes_head_table():
     n = 64
     query = n + n / 4 + 5 * n                                # level bytes, visited init, expansion
     l0 = 8 * 1 + 4 * 2 + (16 + 1 + 8 + 4) * 2                # items, ids, per found: head, byte, item, queue
     l1 = (n / 8 + 4 * 2) + (3 * n / 8 + 16 * 5 + 4 * max(0, 10 - 2 * 5) + 3)
     l2 = (n / 8 + (16 + 8) * 3) + (8 * 3 + 4 * 6 + 0)
-    assert bench.algorithmic_bytes(n, 8, LEVELS) == pytest.approx(query + l0 + l1 + l2)
+    assert bench.layout_bytes(n, 8, LEVELS) == pytest.approx(query + l0 + l1 + l2)
     assert query + l0 + l1 + l2 == 725
 
 
-def test_algorithmic_bytes_row_pointers_no_queue():
+def test_layout_bytes_row_pointers_no_queue():
     n, rp = 64, 4
     query = n + n / 4 + 5 * n
     l0 = 8 * 1 + 4 * 2 + (2 * rp + 1 + 8) * 2
     l1 = (n / 8 + 4 * 2) + (3 * n / 8 + rp * 5 + 4 * 10 + 3)
     l2 = (n / 8 + (2 * rp + 8) * 3) + (8 * 3 + 4 * 6)
-    got = bench.algorithmic_bytes(n, rp, LEVELS, head=False, queue=False)
+    got = bench.layout_bytes(n, rp, LEVELS, head=False, queue=False)
     assert got == pytest.approx(query + l0 + l1 + l2)
     assert got == 657  # 400 + 50 + 103 + 104
