@@ -530,7 +530,8 @@ def run_large(args):
     Per graph: 8 seeded sources; top-down only (the paper's large-diameter path,
     Section 3) as one persistent launch, as a replayed CUDA graph of it, and as
     one launch per level with the host reading the frontier size, to show what
-    the grid barrier saves.
+    the grid barrier saves; and the multi-level local expansion (several levels
+    per grid barrier, Section 2's "other optimization" (c)).
     """
     import torch
 
@@ -552,8 +553,9 @@ def run_large(args):
             reached = st["reached"]
         rec["levels_mean"] = float(np.mean(levels))
         rec["reached_last"] = int(reached)
-        for lname, launch in (("persistent", 0), ("graph", 2), ("per_level", 1)):
-            p = bfs.make_params(policy=3, launch=launch)
+        for lname, policy, launch in (("persistent", 3, 0), ("graph", 3, 2), ("per_level", 3, 1),
+                                      ("local", bfs.BFS_POLICY_LOCAL, 0)):
+            p = bfs.make_params(policy=policy, launch=launch)
             bfs.bfs_single_ex(g, int(srcs[0]), d, params=p)
             torch.cuda.synchronize()
             e0, e1 = _events()
@@ -567,10 +569,13 @@ def run_large(args):
             rec[lname] = {"ms_per_bfs": ms, "us_per_level": 1e3 * ms / rec["levels_mean"],
                           "wall_ms_per_bfs": 1e3 * (time.perf_counter() - t0) / len(srcs)}
         rec["persistent_speedup_vs_per_level"] = rec["per_level"]["ms_per_bfs"] / rec["persistent"]["ms_per_bfs"]
+        rec["local_speedup_vs_persistent"] = rec["persistent"]["ms_per_bfs"] / rec["local"]["ms_per_bfs"]
         res[name] = rec
         g.free()
-    _json({"metric": "ms per BFS, large-diameter graphs (top-down only), persistent vs per-level launches",
-           "value": res["grid_4096x4096"]["persistent"]["ms_per_bfs"], "unit": "ms", "higher_is_better": False,
+    best = min(res["grid_4096x4096"][k]["ms_per_bfs"] for k in ("persistent", "graph", "local"))
+    _json({"metric": "ms per BFS, large-diameter graphs: level-synchronous top-down (persistent, CUDA graph, "
+                     "per-level launches) and multi-level local expansion",
+           "value": best, "unit": "ms", "higher_is_better": False,
            "n_gpus": 1, "dtype": "int32", "data": "synthetic", "config": {"workload": "large_diameter", **res}})
     return 0
 

@@ -76,6 +76,20 @@ extern "C" {
 #define BFS_POLICY_BU_FROM_1 4 /* top-down at level 0, bottom-up afterwards (testing) */
 #define BFS_POLICY_SCRIPT 5   /* level L is bottom-up iff bit min(L,63) of bfs_params.script is set
                                  (bit 0 is ignored: level 0 is top-down); testing */
+#define BFS_POLICY_LOCAL 6    /* top-down with several levels per grid barrier (Section 2, "Other
+                                 Optimizations" (c): threads advance their own part of the frontier
+                                 for several levels without merging; for Section 3's large-diameter
+                                 graphs).  Each block expands its share of the frontier for up to
+                                 bfs_params.local_levels levels on a shared-memory queue, distances
+                                 are relaxed with atomicMin (a vertex reached first along a longer
+                                 path is corrected and expanded again) and the search stops at the
+                                 fixpoint, so the distances are the same exact values.  Runs as one
+                                 persistent launch (BFS_LAUNCH_GRAPH runs it the same way; with
+                                 BFS_LAUNCH_PER_LEVEL it is BFS_EINVAL); it always runs on the graph
+                                 as uploaded (bfs_params.relabel is ignored).  Level records
+                                 (bfs_single_ex) then describe super-steps: direction 2, frontier =
+                                 global queue entries at its start, found = entries queued for the
+                                 next, edges = entries examined (with stats), ns = device time. */
 
 /* ---- launch modes (bfs_params.launch) ---- */
 #define BFS_LAUNCH_PERSISTENT 0 /* one cooperative launch runs every level, grid barrier between levels */
@@ -135,7 +149,9 @@ typedef struct bfs_params {
                                 first use) so the frontier bits of high-degree vertices share cache
                                 lines; distances are still written in the caller's ids.  0 (default):
                                 the graph as uploaded */
-    int32_t reserved[4];
+    int32_t local_levels;    /* BFS_POLICY_LOCAL: levels a block advances on its own between two grid
+                                barriers (1..4096, default 16) */
+    int32_t reserved[3];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique
@@ -154,7 +170,11 @@ typedef struct bfs_stats {
     int64_t bu_edges;        /* sum over bottom-up levels of entries examined (to the first hit) */
     int64_t bu_found;        /* sum over bottom-up levels of |F_{L+1}| */
     int64_t conv_frontier;   /* sum over conversions of |F| */
-    int64_t reserved[4];
+    int64_t supersteps;      /* BFS_POLICY_LOCAL: grid-synchronised super-steps (0 otherwise) */
+    int64_t improved;        /* BFS_POLICY_LOCAL: successful relaxations (labels lowered), the source
+                                excluded; above reached - 1 when a vertex was first reached along a
+                                longer path (td_frontier: entries expanded, td_edges: examined) */
+    int64_t reserved[2];
 } bfs_stats;
 
 /* One level's counters (optional detail). direction: 0 top-down, 1 bottom-up. */

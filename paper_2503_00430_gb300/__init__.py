@@ -42,6 +42,7 @@ BFS_POLICY_EDGES = 2
 BFS_POLICY_TD_ONLY = 3
 BFS_POLICY_BU_FROM_1 = 4
 BFS_POLICY_SCRIPT = 5
+BFS_POLICY_LOCAL = 6
 
 BFS_LAUNCH_PERSISTENT = 0
 BFS_LAUNCH_PER_LEVEL = 1
@@ -65,7 +66,8 @@ class bfs_params(ctypes.Structure):
         ("test_barrier_extra", ctypes.c_int32), ("bu_chunk", ctypes.c_int32),
         ("bu_thread_max", ctypes.c_int32), ("ms_lanes", ctypes.c_int32), ("ms_ring", ctypes.c_int32),
         ("ms_heavy_min", ctypes.c_int32), ("ms_degree_order", ctypes.c_int32), ("ms_alpha", ctypes.c_int32),
-        ("ms_relabel", ctypes.c_int32), ("relabel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("ms_relabel", ctypes.c_int32), ("relabel", ctypes.c_int32), ("local_levels", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -75,7 +77,7 @@ class bfs_stats(ctypes.Structure):
         ("conversions", ctypes.c_int32), ("reached", ctypes.c_int64), ("edges_reached", ctypes.c_int64),
         ("td_frontier", ctypes.c_int64), ("td_edges", ctypes.c_int64), ("bu_unvisited", ctypes.c_int64),
         ("bu_edges", ctypes.c_int64), ("bu_found", ctypes.c_int64), ("conv_frontier", ctypes.c_int64),
-        ("reserved", ctypes.c_int64 * 4),
+        ("supersteps", ctypes.c_int64), ("improved", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2),
     ]
 
     def as_dict(self) -> dict:
@@ -342,8 +344,9 @@ def bfs_single_ex(g: Graph, src: int, dist, params: bfs_params | None = None, st
     _check(rc, "bfs_single_ex")
     levels = []
     if lv is not None:
-        # every level has a non-empty frontier; unused entries stay zero
-        nl = min(st.levels, level_cap) if st is not None else next(
+        # every level (super-step under BFS_POLICY_LOCAL) has a non-empty frontier; unused entries stay zero
+        nrec = (st.supersteps or st.levels) if st is not None else None
+        nl = min(nrec, level_cap) if nrec is not None else next(
             (i for i in range(level_cap) if lv[i].frontier == 0), level_cap)
         levels = [lv[i].as_dict() for i in range(nl)]
     return (st.as_dict() if st is not None else None), levels

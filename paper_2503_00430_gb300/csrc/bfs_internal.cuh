@@ -36,9 +36,11 @@ struct Ctrl {
   unsigned long long barrier;  // grid-barrier arrival counter
   int status;                  // BFS_OK or BFS_ETIMEOUT
   int levels, td_levels, bu_levels, conversions;
-  int pad[3];
+  int supersteps;              // BFS_POLICY_LOCAL
+  int pad[2];
   unsigned long long reached, edges_reached;
   unsigned long long td_frontier, td_edges, bu_unvisited, bu_edges, bu_found, conv_frontier;
+  unsigned long long improved;  // BFS_POLICY_LOCAL: labels lowered
   Slot slot[4];
 };
 
@@ -220,6 +222,9 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
 int serve_group_launch(ServeGroup* G, int tau_inv);
 int serve_group_ready(ServeGroup* G);
 int serve_group_finish(ServeGroup* G, unsigned long long* retired);
+// Multi-level local expansion (bfs_local.cu): launches the BFS_POLICY_LOCAL kernel.
+int run_local(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st, bfs_level_stat* levels,
+              int level_cap, cudaStream_t stream);
 int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads_per_block,
                                cudaStream_t stream);
 

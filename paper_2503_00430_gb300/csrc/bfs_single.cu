@@ -25,89 +25,15 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include "bfs_device.cuh"
 #include "bfs_internal.cuh"
 
 namespace gbfs {
 
 namespace {
 
-__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
-__device__ __forceinline__ unsigned lanemask_lt() {
-  unsigned r;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
-  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
+using namespace dev;
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// L2 eviction-priority policies: data read once per level (adjacency, head
-// records) is marked evict-first, the small per-vertex state that every level
-// updates (level bytes) evict-last, so the streaming reads do not push it out.
-__device__ __forceinline__ unsigned long long policy_evict_first() {
-  unsigned long long pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ unsigned long long policy_evict_last() {
-  unsigned long long pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-  return pol;
-}
-__device__ __forceinline__ void st_u8_last(unsigned char* p, unsigned v) {
-  asm volatile("st.global.L2::cache_hint.u8 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(policy_evict_last()) : "memory");
-}
-__device__ __forceinline__ void st_v4_last(void* p, unsigned a, unsigned b, unsigned c, unsigned d) {
-  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(a), "r"(b), "r"(c),
-               "r"(d), "l"(policy_evict_last())
-               : "memory");
-}
-// Asynchronous 16-byte global -> shared copy, evict-first in L2 (zero-filled
-// when src_bytes is 0).
-__device__ __forceinline__ void cp_async16_first(void* smem, const void* gmem, int src_bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(sa), "l"(gmem),
-               "r"(src_bytes), "l"(policy_evict_first())
-               : "memory");
-}
-__device__ __forceinline__ int4 ldg4_first(const int* p) {
-  int4 q;
-  asm volatile("ld.global.nc.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w)
-               : "l"(p), "l"(policy_evict_first()));
-  return q;
-}
 
 // The level of vertex v is L + 1: a level byte while the search keeps them
 // (direct = false), else its int32 distance.
@@ -116,65 +42,13 @@ __device__ __forceinline__ void mark_level(const KParams& P, bool direct, int v,
   else st_u8_last(P.lv8 + v, (unsigned)(L + 1));
 }
 
-template <typename RP>
-__device__ __forceinline__ long long rp_at(const void* rp, long long i) {
-  return (long long)__ldg(reinterpret_cast<const RP*>(rp) + i);
-}
-
-__device__ __forceinline__ int warp_incl_scan(int x) {
-  const unsigned lane = lane_id();
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(kFull, x, o);
-    if (lane >= (unsigned)o) x += y;
-  }
-  return x;
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-  return x;
-}
-
 __device__ __forceinline__ unsigned long long pack_item(long long start, int len) {
   return ((unsigned long long)start << 16) | (unsigned long long)(unsigned)len;
 }
 
-// Bounded grid barrier.  Returns false when the query must stop (a wait ran
-// out of time here or elsewhere); then the status word holds BFS_ETIMEOUT.
-__device__ bool grid_barrier(const KParams& P, unsigned& epoch) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ++epoch;
-    const unsigned long long nb = (unsigned long long)gridDim.x + (unsigned long long)P.barrier_extra;
-    const unsigned long long target = (unsigned long long)epoch * nb;
-    red_release_add(&P.ctrl->barrier, 1ull);
-    int ok = 1;
-    unsigned long long t0 = 0;
-    unsigned spins = 0;
-    while (ld_acquire_u64(&P.ctrl->barrier) < target) {
-      if (ld_relaxed_s32(&P.ctrl->status) != 0) {
-        ok = 0;
-        break;
-      }
-      if ((++spins & 63u) == 0) {
-        unsigned long long t = globaltimer_ns();
-        if (t0 == 0) {
-          t0 = t;
-        } else if ((long long)(t - t0) > P.timeout_ns) {
-          atomicCAS(&P.ctrl->status, 0, BFS_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok && ld_relaxed_s32(&P.ctrl->status) == 0;
-  }
-  __syncthreads();
-  return s_ok != 0;
+// Bounded grid barrier of the query's control block.
+__device__ __forceinline__ bool grid_barrier(const KParams& P, unsigned& epoch) {
+  return grid_barrier_ctl(P.ctrl, P.timeout_ns, P.barrier_extra, epoch);
 }
 
 // Per-thread work counters of one phase.
@@ -466,34 +340,6 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, bool direct, 
     }
   }
   append_hubs(P, hubs, s, d, out, mgn);
-}
-
-// Position of the n-th (0-based) set bit of mask, by halving the window with
-// population counts; always in [0, 31].
-__device__ __forceinline__ int nth_set_bit(unsigned mask, int n) {
-  int pos = 0;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const int c = __popc(mask & ((1u << w) - 1u));
-    if (n >= c) {
-      n -= c;
-      mask >>= w;
-      pos += w;
-    }
-  }
-  return pos;
-}
-
-// Lane holding entry e of the concatenation described by the exclusive scan
-// `excl` of 32 lengths (largest lane whose start is <= e).
-__device__ __forceinline__ int owner_of(int excl, int e) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    const int ex = __shfl_sync(kFull, excl, lo + step);
-    if (ex <= e) lo += step;
-  }
-  return lo;
 }
 
 // Warp-collective: visit the entries [s, e) of one adjacency span, 128 per
@@ -1610,9 +1456,13 @@ int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_st
   GBFS_CUDA(cudaStreamWaitEvent(stream, ws.done, 0));
   int rc;
   int launch = p.launch;
+  const bool local = K.policy == BFS_POLICY_LOCAL;
+  if (local && launch == BFS_LAUNCH_PER_LEVEL) return BFS_EINVAL;
   if (launch == BFS_LAUNCH_GRAPH && stats) launch = BFS_LAUNCH_PERSISTENT;
-  if (launch != BFS_LAUNCH_GRAPH) GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
-  if (launch == BFS_LAUNCH_GRAPH) {
+  if (launch != BFS_LAUNCH_GRAPH && !local) GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
+  if (local) {
+    rc = run_local(g, src, dist_dev, p, st, levels, level_cap, stream);
+  } else if (launch == BFS_LAUNCH_GRAPH) {
     rc = g->rp_bits == 32 ? launch_graph<int>(g, K, p, stream) : launch_graph<long long>(g, K, p, stream);
   } else if (launch == BFS_LAUNCH_PER_LEVEL) {
     if (g->rp_bits == 32)
@@ -1646,9 +1496,13 @@ int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_st
     st->bu_edges = (int64_t)c.bu_edges;
     st->bu_found = (int64_t)c.bu_found;
     st->conv_frontier = (int64_t)c.conv_frontier;
+    st->supersteps = local ? c.supersteps : 0;
+    st->improved = local ? (int64_t)c.improved : 0;
+    if (local) st->td_levels = c.levels;
   }
   if (levels && level_cap > 0) {
-    int nl = c.levels < level_cap ? c.levels : level_cap;
+    const int nrec = local ? c.supersteps : c.levels;
+    int nl = nrec < level_cap ? nrec : level_cap;
     GBFS_CUDA(cudaMemcpy(levels, ws.lst, sizeof(bfs_level_stat) * (size_t)nl, cudaMemcpyDeviceToHost));
   }
   return BFS_OK;

@@ -85,7 +85,8 @@ def test_er_2e24_bench_configuration_all_64_sources(bfs):
 
 def test_large_diameter_bench_configuration(bfs):
     """Grid 4096^2 and RGG 2^23, top-down only (the bench's large-diameter runs), all 8 sources,
-    persistent launch and its CUDA-graph replay; the first 2 sources also with one launch per level."""
+    persistent launch, its CUDA-graph replay and the multi-level local expansion; the first 2
+    sources also with one launch per level."""
     for name, make in bench.large_specs():
         rp, col = make()
         srcs = [int(s) for s in graphgen.sources(rp, 8, bench.LARGE_SRC_SEED)]
@@ -93,9 +94,10 @@ def test_large_diameter_bench_configuration(bfs):
         want = oracle.bfs_many(rp, col, srcs, threads=min(THREADS, len(srcs)))
         d = torch.empty(len(rp) - 1, dtype=torch.int32, device="cuda")
         for i, s in enumerate(srcs):
-            for launch in (0, 2) + ((1,) if i < 2 else ()):
-                bfs.bfs_single_ex(g, s, d, params=bfs.make_params(policy=3, launch=launch))
-                assert np.array_equal(d.cpu().numpy(), want[i]), (name, i, launch)
+            for policy, launch in ((3, 0), (3, 2), (bfs.BFS_POLICY_LOCAL, 0)) + (((3, 1),) if i < 2 else ()):
+                d.fill_(77)
+                bfs.bfs_single_ex(g, s, d, params=bfs.make_params(policy=policy, launch=launch))
+                assert np.array_equal(d.cpu().numpy(), want[i]), (name, i, policy, launch)
         g.free()
 
 
