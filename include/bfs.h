@@ -65,8 +65,11 @@ extern "C" {
  * Every policy yields the same distances; they differ only in work.
  * Level 0 is always top-down (Listing 2 starts with is_top_down = true). */
 #define BFS_POLICY_AUTO 0     /* graph class rule of Section 3: average degree m/n below
-                                 bfs_params.large_diameter_degree (7) -> top-down only,
-                                 otherwise BFS_POLICY_EDGES */
+                                 bfs_params.large_diameter_degree (7) -> top-down only, as
+                                 BFS_POLICY_LOCAL when no vertex has more than 4096 entries (a
+                                 longer list would be scanned by one warp there) and the launch is
+                                 not BFS_LAUNCH_PER_LEVEL, as BFS_POLICY_TD_ONLY otherwise; else
+                                 BFS_POLICY_EDGES */
 #define BFS_POLICY_FRONTIER 1 /* the paper's BFS-Hybrid rule (Section 2, Listing 2): next level
                                  is top-down iff tau_inv*|F| < n (the paper's 5%: tau_inv = 20) */
 #define BFS_POLICY_EDGES 2    /* the edge-count rule the paper cites as BFS-Hybrid-dagger
@@ -151,7 +154,10 @@ typedef struct bfs_params {
                                 the graph as uploaded */
     int32_t local_levels;    /* BFS_POLICY_LOCAL: levels a block advances on its own between two grid
                                 barriers (1..4096, default 16) */
-    int32_t reserved[3];
+    int32_t local_threads;   /* BFS_POLICY_LOCAL: threads per block (64..512, multiple of 32, default
+                                64; small blocks take small shares of the frontier, so the levels a
+                                block runs alone are short) */
+    int32_t reserved[2];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique
@@ -501,8 +507,9 @@ void bfs_serve_destroy(bfs_server *srv);
  * All calls share the one array and it keeps the last call's contents: calls
  * that may overlap on the GPU (other streams, unordered host threads) race
  * with each other and must be serialized by the caller.
- * Uses the default parameters (policy AUTO).  Blocks until the query has
- * finished.  Errors: BFS_EINVAL, BFS_ENOMEM (too large), BFS_ECUDA,
+ * Uses the default parameters with the level-synchronous kernel (top-down
+ * only below average degree 7, else the edge-count rule).  Blocks until the
+ * query has finished.  Errors: BFS_EINVAL, BFS_ENOMEM (too large), BFS_ECUDA,
  * BFS_ETIMEOUT.
  */
 int bfs_single_noalloc(const void *row_ptr, int row_ptr_bits, const int32_t *col_idx, int64_t n,

@@ -67,7 +67,7 @@ class bfs_params(ctypes.Structure):
         ("bu_thread_max", ctypes.c_int32), ("ms_lanes", ctypes.c_int32), ("ms_ring", ctypes.c_int32),
         ("ms_heavy_min", ctypes.c_int32), ("ms_degree_order", ctypes.c_int32), ("ms_alpha", ctypes.c_int32),
         ("ms_relabel", ctypes.c_int32), ("relabel", ctypes.c_int32), ("local_levels", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("local_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 

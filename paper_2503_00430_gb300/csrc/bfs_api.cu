@@ -289,6 +289,7 @@ void free_single_ws(bfs_graph* g) {
 static int check_params(const bfs_params& p) {
   if (p.policy < 0 || p.policy > BFS_POLICY_LOCAL) return BFS_EINVAL;
   if (p.local_levels < 1 || p.local_levels > 4096) return BFS_EINVAL;
+  if (p.local_threads < 64 || p.local_threads > 512 || (p.local_threads & 31)) return BFS_EINVAL;
   if (p.launch < 0 || p.launch > BFS_LAUNCH_GRAPH) return BFS_EINVAL;
   if (p.alpha < 1 || p.beta < 1 || p.tau_inv < 1) return BFS_EINVAL;
   if (p.small_max < 1 || p.small_max > 32) return BFS_EINVAL;
@@ -354,6 +355,7 @@ void bfs_params_default(bfs_params* p) {
   p->ms_alpha = 2;
   p->ms_relabel = 1;
   p->local_levels = 16;
+  p->local_threads = 64;
 }
 
 int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n, int64_t m,

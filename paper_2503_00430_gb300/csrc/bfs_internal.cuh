@@ -222,6 +222,9 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
 int serve_group_launch(ServeGroup* G, int tau_inv);
 int serve_group_ready(ServeGroup* G);
 int serve_group_finish(ServeGroup* G, unsigned long long* retired);
+// BFS_POLICY_AUTO picks BFS_POLICY_LOCAL for large-diameter graphs whose longest list is at most
+// this long (the local kernel scans a list with one warp).
+constexpr long long kLocalAutoMaxDegree = 4096;
 // Multi-level local expansion (bfs_local.cu): launches the BFS_POLICY_LOCAL kernel.
 int run_local(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st, bfs_level_stat* levels,
               int level_cap, cudaStream_t stream);

@@ -371,7 +371,10 @@ int run_local(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_sta
   P.qb1 = ws.bm[1];
   P.ctrl = ws.ctrl;
   P.K = p.local_levels;
-  P.cap_local = 1024;
+  // Shared queue slots: 8 per thread (at least 256, at most 1024), so small
+  // blocks stay small enough for many to share an SM.
+  const int threads = p.local_threads;
+  P.cap_local = 8 * threads < 256 ? 256 : (8 * threads > 1024 ? 1024 : 8 * threads);
   P.timeout_ns = (long long)p.timeout_ms * 1000000ll;
   P.barrier_extra = p.test_barrier_extra;
   const bool stats = st != nullptr;
@@ -384,10 +387,6 @@ int run_local(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_sta
   const size_t smem = local_smem(P.cap_local);
   GBFS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  // Blocks of at most kLocalThreads threads (the kernel's launch bound): the
-  // local levels are latency-bound, a block seldom has more than a few warps'
-  // worth of frontier, and the registers go to loads in flight instead.
-  const int threads = p.threads_per_block < kLocalThreads ? p.threads_per_block : kLocalThreads;
   GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
   if (per_sm < 1) return BFS_EINVAL;
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;

@@ -1207,8 +1207,11 @@ static cudaError_t prepare_kernel(const void* fn, int threads_per_block) {
 
 static int resolve_policy(const bfs_graph* g, const bfs_params& p) {
   if (p.policy != BFS_POLICY_AUTO) return p.policy;
-  // Section 3: average degree below 7 marks a large-diameter graph -> top-down only.
-  if ((double)g->m < (double)p.large_diameter_degree * (double)g->n) return BFS_POLICY_TD_ONLY;
+  // Section 3: average degree below 7 marks a large-diameter graph -> top-down only; several
+  // levels per grid barrier unless a long list would hold up one warp of the local kernel.
+  if ((double)g->m < (double)p.large_diameter_degree * (double)g->n)
+    return g->max_deg <= kLocalAutoMaxDegree && p.launch != BFS_LAUNCH_PER_LEVEL ? BFS_POLICY_LOCAL
+                                                                                 : BFS_POLICY_TD_ONLY;
   return BFS_POLICY_EDGES;
 }
 

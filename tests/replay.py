@@ -11,13 +11,19 @@ from __future__ import annotations
 
 import numpy as np
 
-POLICY_FRONTIER, POLICY_EDGES, POLICY_TD_ONLY, POLICY_BU_FROM_1, POLICY_SCRIPT = 1, 2, 3, 4, 5
+POLICY_FRONTIER, POLICY_EDGES, POLICY_TD_ONLY, POLICY_BU_FROM_1, POLICY_SCRIPT, POLICY_LOCAL = 1, 2, 3, 4, 5, 6
+LOCAL_AUTO_MAX_DEGREE = 4096
 
 
-def resolve(policy, n, m, large_diameter_degree=7):
+def resolve(policy, n, m, large_diameter_degree=7, max_degree=0):
+    """The policy BFS_POLICY_AUTO stands for: Section 3's large-diameter class (average degree
+    below 7) runs top-down only, as the multi-level local kernel unless a list is longer than
+    4096 entries; other graphs use the edge-count rule."""
     if policy != 0:
         return policy
-    return POLICY_TD_ONLY if m < large_diameter_degree * n else POLICY_EDGES
+    if m < large_diameter_degree * n:
+        return POLICY_LOCAL if max_degree <= LOCAL_AUTO_MAX_DEGREE else POLICY_TD_ONLY
+    return POLICY_EDGES
 
 
 def next_top_down(policy, nl, cur_td, nf_next, nf_cur, mf_next, m_unv, n, alpha=14, beta=24, tau_inv=20, script=0):
@@ -86,7 +92,9 @@ def replay(row_ptr, col, src, dist, policy=0, alpha=14, beta=24, tau_inv=20, scr
     n = len(row_ptr) - 1
     m = int(row_ptr[-1])
     deg = np.diff(row_ptr)
-    pol = resolve(policy, n, m, large_diameter_degree)
+    pol = resolve(policy, n, m, large_diameter_degree, int(deg.max()) if n else 0)
+    if pol == POLICY_LOCAL:  # per-level launches of AUTO run the level-synchronous top-down path
+        pol = POLICY_TD_ONLY
     ecc = int(dist.max())
     sizes = np.bincount(dist[dist >= 0], minlength=ecc + 2)
     degsum = np.bincount(dist[dist >= 0], weights=deg[dist >= 0], minlength=ecc + 2).astype(np.int64)

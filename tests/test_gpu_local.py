@@ -95,8 +95,8 @@ def test_large_diameter_graphs(bfs):
 
 def test_block_shapes(bfs):
     rp, col = graphgen.grid2d(120, 97)
-    for extra in (dict(threads_per_block=64), dict(threads_per_block=1024, blocks_per_sm=1),
-                  dict(threads_per_block=128, blocks_per_sm=1)):
+    for extra in (dict(local_threads=64), dict(local_threads=512, blocks_per_sm=1),
+                  dict(local_threads=128, blocks_per_sm=1), dict(local_threads=96, blocks_per_sm=3)):
         check(bfs, rp, col, [0, 5000], ks=(8,), rp_bits=32, extra=extra)
 
 
@@ -121,13 +121,31 @@ def test_other_launch_modes(bfs):
         bfs.bfs_single_ex(g, 3, d, params=bfs.make_params(policy=bfs.BFS_POLICY_LOCAL,
                                                          launch=bfs.BFS_LAUNCH_PER_LEVEL))
     assert e.value.code == bfs.BFS_EINVAL
-    for bad in (0, 5000):
+    for bad in (dict(local_levels=0), dict(local_levels=5000), dict(local_threads=32), dict(local_threads=100),
+                dict(local_threads=1024)):
         with pytest.raises(bfs.BfsError) as e:
-            bfs.bfs_single_ex(g, 3, d, params=bfs.make_params(policy=bfs.BFS_POLICY_LOCAL, local_levels=bad))
+            bfs.bfs_single_ex(g, 3, d, params=bfs.make_params(policy=bfs.BFS_POLICY_LOCAL, **bad))
         assert e.value.code == bfs.BFS_EINVAL
     # relabel is ignored: same distances
     bfs.bfs_single_ex(g, 3, d, params=bfs.make_params(policy=bfs.BFS_POLICY_LOCAL, relabel=1))
     assert np.array_equal(d.cpu().numpy(), want)
+    g.free()
+
+
+def test_auto_policy_picks_local_for_large_diameter(bfs):
+    """Average degree below 7 and no list longer than 4096: AUTO runs the local kernel (its
+    counters report super-steps); a star with a longer list stays level-synchronous."""
+    rp, col = graphgen.grid2d(64, 64)
+    g = bfs.bfs_graph_upload(rp, col)
+    d = torch.empty(4096, dtype=torch.int32, device="cuda")
+    st, _ = bfs.bfs_single_ex(g, 0, d, stats=True)
+    assert st["supersteps"] > 0 and np.array_equal(d.cpu().numpy(), oracle.bfs(rp, col, 0))
+    g.free()
+    rp, col = G.star_graph(5000)
+    g = bfs.bfs_graph_upload(rp, col)
+    d = torch.empty(5000, dtype=torch.int32, device="cuda")
+    st, _ = bfs.bfs_single_ex(g, 3, d, stats=True)
+    assert st["supersteps"] == 0 and np.array_equal(d.cpu().numpy(), oracle.bfs(rp, col, 3))
     g.free()
 
 
