@@ -36,10 +36,7 @@ NSRC = 64
 SRC_SEED = 1002
 METRIC = "GTEPS (harmonic mean, 64 sources) R-MAT s25; BFS queries/s & p99 latency"
 L2_BYTES = 129 * 1024 * 1024
-# Single-source queries on the degree-renumbered copy (bfs_params.relabel): the default for the
-# skewed R-MAT workload (its hubs' frontier bits then share cache lines: -33 % DRAM traffic), not
-# for the uniform random graph, whose degrees are all alike (there it costs 3 %).
-RELABEL_DEFAULT = {"rmat25": 1, "er24": 0}
+TUNED_TABLE = os.path.join(ROOT, "paper_2503_00430_gb300", "tuned.json")
 
 
 def peaks():
@@ -99,9 +96,15 @@ def upload_flags(bfs, args):
     return bfs.BFS_VALIDATE | (0 if args.no_degree_order else bfs.BFS_DEGREE_ORDER)
 
 
-def query_params(bfs, args):
-    """bfs_params of the timed single-source queries."""
-    return bfs.make_params(policy=args.policy, launch=args.launch, relabel=args.relabel)
+def query_params(bfs, args, n=0, m=0):
+    """bfs_params of the timed single-source queries: the tuning table's entry for the graph's
+    class (defaults where it has none), then any policy / launch / relabel given on the command line."""
+    p = bfs.bfs_params_default() if args.no_tuned else bfs.tuned_params(None, None, "single", n, m)
+    for k in ("policy", "launch", "relabel"):
+        v = getattr(args, k)
+        if v is not None:
+            setattr(p, k, v)
+    return p
 
 
 def parse_args(argv=None):
@@ -111,16 +114,18 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=SCALE)
-    ap.add_argument("--policy", type=int, default=0)
-    ap.add_argument("--launch", type=int, default=0)
+    ap.add_argument("--policy", type=int, default=None, help="direction policy (default: tuning table, else AUTO)")
+    ap.add_argument("--launch", type=int, default=None, help="launch mode (default: tuning table, else persistent)")
     ap.add_argument("--relabel", type=int, default=None, choices=[0, 1],
-                    help="single-source queries on the degree-renumbered copy of the graph")
+                    help="single-source queries on the degree-renumbered copy of the graph (default: tuning table)")
+    ap.add_argument("--no-tuned", action="store_true", help="library defaults instead of the tuning table")
+    ap.add_argument("--tune-out", default=None, help="tune: table to write (default: the package's tuned.json)")
     ap.add_argument("--cpu-sample", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-degree-order", action="store_true",
                     help="keep the generator's id-sorted adjacency order on the device")
     ap.add_argument("--workload", default="rmat25",
-                    choices=["rmat25", "er24", "large", "msbfs", "graphset", "serve", "dup"])
+                    choices=["rmat25", "er24", "large", "msbfs", "graphset", "serve", "dup", "tune"])
     ap.add_argument("--graphs", type=int, default=10000, help="graphset: graphs in the set")
     ap.add_argument("--serve-queries", type=int, default=10000, help="serve: queries per offered rate")
     ap.add_argument("--no-msbfs", action="store_true",
@@ -128,8 +133,6 @@ def parse_args(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
-    if args.relabel is None:
-        args.relabel = RELABEL_DEFAULT.get(args.workload, 0)
     return args
 
 
@@ -361,9 +364,10 @@ def run_ours(args):
     t_gen = time.perf_counter() - t_gen
     n, m = len(rp) - 1, len(col)
     g = bfs.bfs_graph_upload(rp, col, flags=upload_flags(bfs, args))
-    params = query_params(bfs, args)
+    params = query_params(bfs, args, n, m)
     has_head = m < (1 << 31) - 8  # the library builds the head table when list starts fit int32
-    hybrid = not (args.policy == bfs.BFS_POLICY_TD_ONLY or (args.policy == bfs.BFS_POLICY_AUTO and m < 7 * n))
+    hybrid = not (params.policy in (bfs.BFS_POLICY_TD_ONLY, bfs.BFS_POLICY_LOCAL)
+                  or (params.policy == bfs.BFS_POLICY_AUTO and m < 7 * n))
     stream = torch.cuda.Stream()
     dist_buf = torch.empty(n, dtype=torch.int32, device="cuda")
 
@@ -415,7 +419,7 @@ def run_ours(args):
     # this workload), and its ratio to the algorithmic bytes of the captured sources.
     traffic, traffic_ratio = None, None
     default_run = (args.scale == SCALE and args.workload == "rmat25" and not args.no_degree_order
-                   and args.policy == 0 and args.launch == 0 and args.relabel == RELABEL_DEFAULT["rmat25"])
+                   and args.policy is None and args.launch is None and args.relabel is None and not args.no_tuned)
     mt = measured_traffic() if default_run else None
     if mt is not None:
         traffic = mt[0]
@@ -448,10 +452,13 @@ def run_ours(args):
                    "edgefactor": EDGEFACTOR, "abcd": [0.57, 0.19, 0.19, 0.05] if args.workload == "rmat25" else None,
                    "n": n, "m": m, "row_ptr": "int64" if rp_bytes == 8 else "int32", "sources": len(srcs),
                    "source_seed": SRC_SEED,
-                   "policy": {0: "auto", 1: "frontier", 2: "edges", 3: "td_only"}.get(args.policy, str(args.policy)),
-                   "launch": {0: "persistent", 1: "per_level", 2: "graph"}[args.launch],
+                   "policy": {0: "auto", 1: "frontier", 2: "edges", 3: "td_only", 6: "local"}.get(params.policy,
+                                                                                                 str(params.policy)),
+                   "launch": {0: "persistent", 1: "per_level", 2: "graph"}[params.launch],
                    "adjacency_order": "id" if args.no_degree_order else "degree_desc",
-                   "vertex_ids": "degree_renumbered_copy" if args.relabel else "as_uploaded",
+                   "vertex_ids": "degree_renumbered_copy" if params.relabel else "as_uploaded",
+                   "params": "library defaults" if args.no_tuned else
+                   f"tuning table entry {bfs.table_key('single', n, m)} (defaults where absent)",
                    "l2": "inputs larger than L2 (4.3 GB neighbour ids), no flush",
                    "step": "64 single-source BFS, each timed with CUDA events",
                    "graph_gen_s": round(t_gen, 1)},
@@ -602,15 +609,16 @@ def run_msbfs(args):
     torch.cuda.synchronize()
     single_s = e0.elapsed_time(e1) / 1e3 / len(srcs)
     out = {"single_source_bfs_per_s": 1.0 / single_s}
+    mp = bfs.bfs_params_default() if args.no_tuned else bfs.tuned_params(None, g, "multi")
     for bits in (8, 32):
         buf = torch.empty((256, n), dtype=torch.uint8 if bits == 8 else torch.int32, device="cuda")
-        st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits)
+        st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits, params=mp)
         torch.cuda.synchronize()
         e0, e1 = _events()
         e0.record()
         reps = max(1, args.steps // 4)
         for _ in range(reps):
-            st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits)
+            st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits, params=mp)
         e1.record()
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3 / reps
@@ -634,13 +642,14 @@ def run_graphset(args):
     gs = graphgen.graph_set(count, 1000, 100000, 8.0, seed=4)
     s = bfs.bfs_graphset_upload(gs.voff, gs.eoff, gs.row_ptr, gs.col)
     dist = torch.empty(int(gs.voff[-1]), dtype=torch.int32, device="cuda")
-    st = bfs.bfs_graphset_run(s, gs.src, dist)
+    gp = bfs.bfs_params_default() if args.no_tuned else bfs.tuned_params(None, None, "graphset")
+    st = bfs.bfs_graphset_run(s, gs.src, dist, params=gp)
     torch.cuda.synchronize()
     reps = max(3, args.steps)
     e0, e1 = _events()
     e0.record()
     for _ in range(reps):
-        st = bfs.bfs_graphset_run(s, gs.src, dist)
+        st = bfs.bfs_graphset_run(s, gs.src, dist, params=gp)
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / reps
@@ -836,6 +845,50 @@ def run_dup(args):
     return 0
 
 
+def run_tune(args):
+    """Autotune the bench workloads and write the tuning table (paper_2503_00430_gb300/tuned.json):
+    single-source parameters on R-MAT s25 (all 64 sources), the uniform random 2^24 graph (64
+    sources) and the 4096^2 grid (8 sources); multi-source parameters on R-MAT s24 (one call over
+    its 256 sources); graph-set launch parameters on the 10,000-graph set.  Every tuner checks that
+    each setting reproduces the starting setting's output exactly."""
+    import torch
+
+    import graphgen
+    import paper_2503_00430_gb300 as bfs
+    torch.cuda.set_device(0)
+    path = args.tune_out or TUNED_TABLE
+    done = {}
+    for wl in ("rmat25", "er24"):
+        a = parse_args(["--workload", wl, "--no-tuned"])
+        rp, col, srcs, _, wname = make_workload(a)
+        g = bfs.bfs_graph_upload(rp, col, flags=upload_flags(bfs, a))
+        p, rep = bfs.bfs_tune(g, srcs)
+        done[wname] = bfs.tune_table_store(path, "single", p, rep, g.n, g.m, wname)
+        g.free()
+        del rp, col
+    name, make = large_specs()[0]
+    rp, col = make()
+    g = bfs.bfs_graph_upload(rp.astype(np.int32), col, flags=bfs.BFS_VALIDATE)
+    p, rep = bfs.bfs_tune(g, graphgen.sources(rp, 8, LARGE_SRC_SEED))
+    done[name] = bfs.tune_table_store(path, "single", p, rep, g.n, g.m, name)
+    g.free()
+    rp, col, srcs = msbfs_workload()
+    g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | bfs.BFS_DEGREE_ORDER)
+    p, rep = bfs.bfs_tune_multi(g, srcs, 8)
+    done["msbfs_rmat_s24_256src"] = bfs.tune_table_store(path, "multi", p, rep, g.n, g.m, "msbfs_rmat_s24_256src")
+    g.free()
+    del rp, col
+    gs = graphgen.graph_set(10000, 1000, 100000, 8.0, seed=4)
+    s = bfs.bfs_graphset_upload(gs.voff, gs.eoff, gs.row_ptr, gs.col)
+    p, rep = bfs.bfs_tune_graphset(s, gs.src)
+    done["graphset_10000"] = bfs.tune_table_store(path, "graphset", p, rep, workload="graphset_10000_er_1e3_1e5_d8")
+    s.free()
+    _json({"metric": "autotuned parameters of the bench workloads", "value": len(done), "unit": "entries",
+           "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+           "config": {"workload": "tune", "table": os.path.relpath(path, ROOT), **done}})
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -843,7 +896,7 @@ def main(argv=None):
     if args.workload in ("rmat25", "er24"):
         return run_ours(args)
     return {"large": run_large, "msbfs": run_msbfs, "graphset": run_graphset, "serve": run_serve,
-            "dup": run_dup}[args.workload](args)
+            "dup": run_dup, "tune": run_tune}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -157,7 +157,9 @@ typedef struct bfs_params {
     int32_t local_threads;   /* BFS_POLICY_LOCAL: threads per block (64..512, multiple of 32, default
                                 64; small blocks take small shares of the frontier, so the levels a
                                 block runs alone are short) */
-    int32_t reserved[2];
+    int32_t serve_queue;     /* bfs_serve_*: queries submitted and not yet admitted before
+                                bfs_serve_submit returns BFS_EAGAIN (0 = default 2^20) */
+    int32_t reserved[1];
 } bfs_params;
 
 /* Per-query work counters (exact, deterministic: the frontier sets are unique
@@ -180,7 +182,10 @@ typedef struct bfs_stats {
     int64_t improved;        /* BFS_POLICY_LOCAL: successful relaxations (labels lowered), the source
                                 excluded; above reached - 1 when a vertex was first reached along a
                                 longer path (td_frontier: entries expanded, td_edges: examined) */
-    int64_t reserved[2];
+    int64_t init_ns;         /* persistent level-synchronous launch: device time from kernel entry to
+                                the end of the per-query init (the counting variant's clock) */
+    int64_t finish_ns;       /* ... and from the end of the last level to the end of the final
+                                level-byte -> int32 expansion (0 where there is none) */
 } bfs_stats;
 
 /* One level's counters (optional detail). direction: 0 top-down, 1 bottom-up. */
@@ -355,22 +360,49 @@ typedef struct bfs_tune_report {
 } bfs_tune_report;
 
 /*
- * Pick single-source parameters for graph g by coordinate descent: policy
- * (Section 2's frontier rule, the edge-count rule, top-down only), alpha, beta,
- * tau_inv, chunk, small_max, bu_thread_max, bu_warp_min, bu_chunk and
- * threads_per_block are tried one field at a time (two sweeps); each setting is
- * timed as the median over the k sample sources (CUDA events, after one warm
- * run per source) and kept when it is at least 2% faster.  Every setting's
- * distances must hash identically to the starting setting's; a mismatch
- * aborts with BFS_ECUDA.  base = NULL starts from the defaults.
+ * Pick single-source parameters for graph g by coordinate descent, one field
+ * at a time (two sweeps).  Small-world graphs (average degree >= 7): policy
+ * (Section 2's frontier rule or the edge-count rule), alpha, beta, tau_inv,
+ * relabel, chunk, small_max, bu_thread_max, bu_warp_min, bu_chunk,
+ * threads_per_block, blocks_per_sm.  Section 3's large-diameter class:
+ * policy (top-down level-synchronous or BFS_POLICY_LOCAL), local_levels,
+ * local_threads, chunk, threads_per_block, blocks_per_sm.  A setting's time is
+ * the mean over the k sample sources of each source's best of three timed
+ * runs (CUDA events, after a warm-up run); it is kept when at least 2% faster.
+ * Every setting's distances must hash identically to the starting setting's;
+ * a mismatch aborts with BFS_ECUDA.  base = NULL starts from the defaults.
  * Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ETIMEOUT.
  */
 int bfs_tune(bfs_graph *g, const int32_t *srcs, int32_t k, const bfs_params *base, bfs_params *out,
              bfs_tune_report *report);
 
+/*
+ * Pick bfs_multi (and serving-group) parameters for graph g: ms_alpha (the
+ * push -> pull switch), ms_heavy_min, ms_ring, ms_lanes, ms_relabel and
+ * ms_degree_order, by the same coordinate descent; a setting's time is the
+ * best of three timed bfs_multi calls on all k sources (dist_bits 8 or 32),
+ * whose whole output must hash identically across settings.  Needs k*n*
+ * dist_bits/8 bytes of device memory for the output.
+ * Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ERANGE.
+ */
+int bfs_tune_multi(bfs_graph *g, const int32_t *srcs, int32_t k, int dist_bits, const bfs_params *base,
+                   bfs_params *out, bfs_tune_report *report);
+
+typedef struct bfs_graphset bfs_graphset;
+
+/*
+ * Pick graph-set parameters (threads_per_block <= 512, blocks_per_sm, alpha,
+ * beta of the block-local direction rule) for one bfs_graphset_run over set s
+ * from srcs (one local source per graph); a setting's time is the best of
+ * three timed runs, whose distances must hash identically across settings.
+ * Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA.
+ */
+int bfs_tune_graphset(bfs_graphset *s, const int32_t *srcs, const bfs_params *base, bfs_params *out,
+                      bfs_tune_report *report);
+
 /* ---- graph sets: many small graphs, one source each, one launch ---- */
 
-typedef struct bfs_graphset bfs_graphset; /* opaque; owned by the library */
+/* bfs_graphset (declared above) is opaque and owned by the library. */
 
 /* Counters of one bfs_graphset_run. */
 typedef struct bfs_graphset_stats {
@@ -442,12 +474,21 @@ typedef struct bfs_query_stats {
  * batching).  Admission is bounded by mem_budget bytes of device memory: a
  * graph's group state (about (8*(2+ms_ring) + 16) bytes per vertex) when its
  * first query arrives, and a 4n-byte staging buffer for every running query
- * whose output is host memory.  Uses params->ms_ring, ms_heavy_min, tau_inv
+ * whose output is host memory.  When a graph's queries cannot be admitted
+ * because other groups hold the budget, those groups stop admitting, finish
+ * their running queries and release their memory, so every graph is served
+ * in turn even when the budget holds one group at a time; a query whose
+ * group alone exceeds the budget completes with status BFS_ENOMEM.  A device
+ * wait that runs out (BFS_ETIMEOUT) fails the running queries of that group
+ * only (their status), the group is rebuilt for the next query, and the
+ * server keeps serving; a CUDA error makes later calls return it.  Uses params->ms_ring, ms_heavy_min, tau_inv
  * (levels run push when tau_inv * |F| < n, else pull) and large_diameter_degree:
  * a graph with m < large_diameter_degree * n (Section 3's large-diameter class)
  * gets a high-priority stream, writes each distance as it is found, and runs
- * consecutive push levels in one persistent launch (bounded device waits:
- * BFS_ETIMEOUT if one runs out).  Every graph has its own worker thread.
+ * consecutive push levels in one persistent launch (bounded device waits of
+ * params->timeout_ms each; params->test_barrier_extra as in bfs_params).
+ * params->serve_queue bounds the submitted, not yet admitted queries.  Every
+ * graph has its own worker thread.
  * NULL params = defaults.
  */
 int bfs_serve_create(size_t mem_budget, const bfs_params *params, bfs_server **out);

@@ -67,7 +67,7 @@ class bfs_params(ctypes.Structure):
         ("bu_thread_max", ctypes.c_int32), ("ms_lanes", ctypes.c_int32), ("ms_ring", ctypes.c_int32),
         ("ms_heavy_min", ctypes.c_int32), ("ms_degree_order", ctypes.c_int32), ("ms_alpha", ctypes.c_int32),
         ("ms_relabel", ctypes.c_int32), ("relabel", ctypes.c_int32), ("local_levels", ctypes.c_int32),
-        ("local_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("local_threads", ctypes.c_int32), ("serve_queue", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -77,7 +77,8 @@ class bfs_stats(ctypes.Structure):
         ("conversions", ctypes.c_int32), ("reached", ctypes.c_int64), ("edges_reached", ctypes.c_int64),
         ("td_frontier", ctypes.c_int64), ("td_edges", ctypes.c_int64), ("bu_unvisited", ctypes.c_int64),
         ("bu_edges", ctypes.c_int64), ("bu_found", ctypes.c_int64), ("conv_frontier", ctypes.c_int64),
-        ("supersteps", ctypes.c_int64), ("improved", ctypes.c_int64), ("reserved", ctypes.c_int64 * 2),
+        ("supersteps", ctypes.c_int64), ("improved", ctypes.c_int64), ("init_ns", ctypes.c_int64),
+        ("finish_ns", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -183,6 +184,10 @@ _SIGNATURES = [
                                         ctypes.POINTER(bfs_graphset_stats), _vp]),
     ("bfs_tune", ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_params),
                                 ctypes.POINTER(bfs_tune_report)]),
+    ("bfs_tune_multi", ctypes.c_int, [_vp, _vp, _i32, ctypes.c_int, ctypes.POINTER(bfs_params),
+                                      ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_tune_report)]),
+    ("bfs_tune_graphset", ctypes.c_int, [_vp, _vp, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_params),
+                                         ctypes.POINTER(bfs_tune_report)]),
     ("bfs_serve_create", ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(bfs_params), ctypes.POINTER(_vp)]),
     ("bfs_serve_add_graph", ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i32)]),
     ("bfs_serve_submit", ctypes.c_int, [_vp, _i32, _i32, _vp, ctypes.POINTER(_u64)]),
@@ -512,8 +517,10 @@ def bfs_serve_destroy(srv: Server):
     srv.destroy()
 
 
-TUNABLE_FIELDS = ("policy", "alpha", "beta", "tau_inv", "chunk", "small_max", "bu_thread_max", "bu_warp_min",
-                  "bu_chunk", "threads_per_block")
+TUNABLE_FIELDS = ("policy", "alpha", "beta", "tau_inv", "relabel", "chunk", "small_max", "bu_thread_max",
+                  "bu_warp_min", "bu_chunk", "threads_per_block", "blocks_per_sm", "local_levels", "local_threads")
+TUNABLE_MULTI_FIELDS = ("ms_alpha", "ms_heavy_min", "ms_ring", "ms_lanes", "ms_relabel", "ms_degree_order")
+TUNABLE_GRAPHSET_FIELDS = ("threads_per_block", "blocks_per_sm", "alpha", "beta")
 
 
 def params_to_dict(p: bfs_params) -> dict:
@@ -530,6 +537,27 @@ def bfs_tune(g: Graph, srcs, base: bfs_params | None = None):
     return out, rep.as_dict()
 
 
+def bfs_tune_multi(g: Graph, srcs, dist_bits: int = 8, base: bfs_params | None = None):
+    """Autotune multi-source (and serving-group) parameters on one call over ``srcs``; returns (params, report)."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.int32)
+    out = bfs_params()
+    rep = bfs_tune_report()
+    _check(load().bfs_tune_multi(g.handle, _ptr(srcs), len(srcs), dist_bits,
+                                 ctypes.byref(base) if base is not None else None, ctypes.byref(out),
+                                 ctypes.byref(rep)), "bfs_tune_multi")
+    return out, rep.as_dict()
+
+
+def bfs_tune_graphset(s: GraphSet, srcs, base: bfs_params | None = None):
+    """Autotune graph-set launch parameters for one run over the set; returns (params, report)."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.int32)
+    out = bfs_params()
+    rep = bfs_tune_report()
+    _check(load().bfs_tune_graphset(s.handle, _ptr(srcs), ctypes.byref(base) if base is not None else None,
+                                    ctypes.byref(out), ctypes.byref(rep)), "bfs_tune_graphset")
+    return out, rep.as_dict()
+
+
 def graph_class(n: int, m: int) -> str:
     """Key of the tuning table: the paper's degree classes (Section 3: average degree below 7
     is large-diameter) split further by size."""
@@ -538,28 +566,47 @@ def graph_class(n: int, m: int) -> str:
     return f"{deg}_n2e{max(0, int(np.log2(max(n, 1))))}"
 
 
-def tune_table_update(path: str, g: Graph, srcs) -> dict:
-    """Tune g and store the result under its graph class in a JSON table at ``path``."""
+TUNED_TABLE = os.path.join(_HERE, "tuned.json")
+_KIND_FIELDS = {"single": TUNABLE_FIELDS, "multi": TUNABLE_MULTI_FIELDS, "graphset": TUNABLE_GRAPHSET_FIELDS}
+
+
+def table_key(kind: str, n: int = 0, m: int = 0) -> str:
+    """Entry of the tuning table: graph sets have one entry, graphs one per class and kind."""
+    return "graphset" if kind == "graphset" else f"{kind}/{graph_class(n, m)}"
+
+
+def tune_table_store(path: str, kind: str, params: bfs_params, report: dict, n: int = 0, m: int = 0,
+                     workload: str = "") -> dict:
+    """Store tuned parameters of one kind ("single", "multi", "graphset") in the JSON table at ``path``."""
     import json
-    params, rep = bfs_tune(g, srcs)
     table = {}
     if os.path.exists(path):
         with open(path) as f:
             table = json.load(f)
-    key = graph_class(g.n, g.m)
-    table[key] = {"params": {k: getattr(params, k) for k in TUNABLE_FIELDS}, "report": rep}
+    entry = {"params": {k: getattr(params, k) for k in _KIND_FIELDS[kind]}, "report": report, "workload": workload}
+    table[table_key(kind, n, m)] = entry
     with open(path, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
-    return table[key]
+    return entry
 
 
-def tuned_params(path: str, g: Graph) -> bfs_params:
-    """Defaults overridden by the table entry of g's class (defaults when absent)."""
+def tune_table_update(path: str, g: Graph, srcs) -> dict:
+    """Tune g's single-source parameters and store them under its graph class."""
+    params, rep = bfs_tune(g, srcs)
+    return tune_table_store(path, "single", params, rep, g.n, g.m)
+
+
+def tuned_params(path: str | None = None, g: Graph | None = None, kind: str = "single", n: int = 0,
+                 m: int = 0) -> bfs_params:
+    """Defaults overridden by the table entry of g's class and ``kind`` (defaults when absent)."""
     import json
+    path = path or TUNED_TABLE
+    if g is not None:
+        n, m = g.n, g.m
     p = bfs_params_default()
     if os.path.exists(path):
         with open(path) as f:
-            entry = json.load(f).get(graph_class(g.n, g.m))
+            entry = json.load(f).get(table_key(kind, n, m))
         if entry:
             for k, v in entry["params"].items():
                 setattr(p, k, v)

@@ -279,6 +279,15 @@ int bfs_graphset_upload(const int64_t* voff, const int64_t* eoff, const int64_t*
   return BFS_OK;
 }
 
+}  // extern "C"
+
+namespace gbfs {
+long long graphset_total_vertices(const bfs_graphset* s) { return s->total_v; }
+int graphset_count(const bfs_graphset* s) { return s->count; }
+}  // namespace gbfs
+
+extern "C" {
+
 void bfs_graphset_free(bfs_graphset* s) {
   if (!s) return;
   cudaDeviceSynchronize();

@@ -41,6 +41,9 @@ struct Ctrl {
   unsigned long long reached, edges_reached;
   unsigned long long td_frontier, td_edges, bu_unvisited, bu_edges, bu_found, conv_frontier;
   unsigned long long improved;  // BFS_POLICY_LOCAL: labels lowered
+  unsigned long long t_begin, t_levels, t_levels_end, t_end;  // device clock: kernel entry, end of init,
+                                                              // end of the last level, end of the final
+                                                              // expansion (block 0's view)
   Slot slot[4];
 };
 
@@ -80,8 +83,10 @@ struct KParams {
   // Degree-renumbered graph (single-source queries with params->relabel): the
   // search runs in new ids; dist is written in the caller's ids through these
   // maps.  Null: the graph as uploaded.
-  const int* new_of = nullptr;   // [n] caller id -> new id (expansion of the level bytes)
-  const int* old_of = nullptr;   // [n] new id -> caller id (direct int32 writes past level 254)
+  const int* new_of = nullptr;   // [n] caller id -> new id
+  const int* old_of = nullptr;   // [n] new id -> caller id: level bytes and distances are written at
+                                 // the caller's id of a found vertex
+  int src_out = 0;               // the source's caller id (= src on the graph as uploaded)
 };
 
 // Direction of level `next_level` (true = top-down), from the counters of the
@@ -219,9 +224,12 @@ cudaStream_t serve_group_stream(ServeGroup* G);
 unsigned long long serve_group_lanes(const ServeGroup* G);
 int serve_group_level(const ServeGroup* G);
 int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* srcs, int* const* outs);
-int serve_group_launch(ServeGroup* G, int tau_inv);
+int serve_group_launch(ServeGroup* G, int tau_inv, long long timeout_ns, int barrier_extra);
 int serve_group_ready(ServeGroup* G);
 int serve_group_finish(ServeGroup* G, unsigned long long* retired);
+// Graph-set facts for the tuner (bfs_graphset.cu).
+long long graphset_total_vertices(const bfs_graphset* s);
+int graphset_count(const bfs_graphset* s);
 // BFS_POLICY_AUTO picks BFS_POLICY_LOCAL for large-diameter graphs whose longest list is at most
 // this long (the local kernel scans a list with one warp).
 constexpr long long kLocalAutoMaxDegree = 4096;

@@ -1449,12 +1449,13 @@ void serve_step(ServeGroup* G, bool push) {
 
 // Grid barrier of the persistent serving launch: arrival with a release add,
 // a bounded acquire spin; on timeout the status is set and every block returns.
-__device__ bool loop_barrier(ServeLoop* SL, unsigned& epoch, long long timeout_ns) {
+// `extra` (testing) makes it wait for that many blocks more than were launched.
+__device__ bool loop_barrier(ServeLoop* SL, unsigned& epoch, long long timeout_ns, int extra) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ++epoch;
-    const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+    const unsigned long long target = (unsigned long long)epoch * ((unsigned long long)gridDim.x + (unsigned)extra);
     __threadfence();
     asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&SL->barrier) : "memory");
     int ok = 1;
@@ -1497,7 +1498,8 @@ __device__ bool loop_barrier(ServeLoop* SL, unsigned& epoch, long long timeout_n
 template <typename RP>
 __global__ void __launch_bounds__(256) k_serve_loop(MsArgs A, unsigned long long* F, int ring, int L0, int* q0,
                                                     int* q1, int qc0, long long nf0, long long mf0, int max_levels,
-                                                    int tau_inv, long long timeout_ns, int need_plan, ServeLoop* SL) {
+                                                    int tau_inv, long long timeout_ns, int need_plan, ServeLoop* SL,
+                                                    int barrier_extra) {
   unsigned epoch = 0;
   const unsigned long long lanes = A.full[0];
   unsigned long long act = A.act[0];
@@ -1515,11 +1517,11 @@ __global__ void __launch_bounds__(256) k_serve_loop(MsArgs A, unsigned long long
     A.out_level = L + 1;
     ms_zero_body(A.Fnext, A.n);
     if (need_plan) ms_push_plan_body<RP>(A, nf);  // only vertices of more than kMsPushChunk entries
-    if (!loop_barrier(SL, epoch, timeout_ns)) return;
+    if (!loop_barrier(SL, epoch, timeout_ns, barrier_extra)) return;
     ms_push_body<1, RP>(A, nf);
-    if (!loop_barrier(SL, epoch, timeout_ns)) return;
+    if (!loop_barrier(SL, epoch, timeout_ns, barrier_extra)) return;
     ms_apply_body<1, RP>(A);
-    if (!loop_barrier(SL, epoch, timeout_ns)) return;
+    if (!loop_barrier(SL, epoch, timeout_ns, barrier_extra)) return;
     const long long nf2 = (long long)ld_cg_u64(&C->nf);
     const unsigned long long act2 = ld_cg_u64(&C->act[0]) & lanes;
     ++it;
@@ -1720,7 +1722,7 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
   return BFS_OK;
 }
 
-int serve_group_launch(ServeGroup* G, int tau_inv) {
+int serve_group_launch(ServeGroup* G, int tau_inv, long long timeout_ns, int barrier_extra) {
   if (!G->lanes || G->launched) return BFS_OK;
   if (!G->direct && G->L + 1 - G->flushed >= G->ring) {
     const int rc = serve_flush(G, G->L);
@@ -1738,11 +1740,11 @@ int serve_group_launch(ServeGroup* G, int tau_inv) {
     int max_levels = G->direct ? (G->lanes == ~0ull ? 4096 : 64) : G->ring - 1 - (G->L - G->flushed);
     int* q0 = G->q[0];
     int* q1 = G->q[1];
-    long long nf0 = G->nf, mf0 = G->mf, timeout_ns = 10000000000ll;
+    long long nf0 = G->nf, mf0 = G->mf;
     ServeLoop* SL = G->SL;
     int need_plan = G->g->max_deg > kMsPushChunk ? 1 : 0;
     void* args[] = {&A,  &F,          &ring,    &L0,         &q0,        &q1, &qc0,
-                    &nf0, &mf0,       &max_levels, &tau_inv, &timeout_ns, &need_plan, &SL};
+                    &nf0, &mf0,       &max_levels, &tau_inv, &timeout_ns, &need_plan, &SL, &barrier_extra};
     GBFS_CUDA(cudaMemsetAsync(G->SL, 0, sizeof(ServeLoop), G->stream));
     const void* fn = G->g->rp_bits == 32 ? reinterpret_cast<const void*>(&k_serve_loop<int>)
                                          : reinterpret_cast<const void*>(&k_serve_loop<long long>);

@@ -14,6 +14,14 @@
 // Section 3) run thousands of short levels: their group's stream gets the
 // highest priority, so its small kernels are scheduled ahead of the dense
 // levels of other groups instead of queueing behind them.
+//
+// Memory pressure: a graph whose group (or a query's staging buffer) does not
+// fit the budget registers as blocked.  While any graph is blocked, every
+// other worker stops admitting, lets its running queries finish and then
+// releases its group and staging buffers, so the blocked graph gets the
+// memory; the released graph's own queries then wait their turn the same way.
+// A device wait that runs out in a group fails that group's running queries
+// (status BFS_ETIMEOUT) and frees the group; the server keeps serving.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -55,6 +63,8 @@ struct Query {
 struct GraphEntry {
   bfs_graph* g = nullptr;
   gbfs::ServeGroup* grp = nullptr;
+  size_t grp_bytes = 0;               // budget bytes the group holds
+  bool mem_blocked = false;           // counted in bfs_server::mem_blocked (guarded by the server mutex)
   std::deque<Query*> pending;         // submitted, not yet taken by the worker (guarded by the server mutex)
   std::condition_variable cv;         // wakes the worker (with the server mutex)
   // Owned by the worker thread:
@@ -78,6 +88,7 @@ struct bfs_server {
   std::condition_variable cv_done;
   size_t queued = 0;                  // submitted, not yet admitted
   size_t queue_cap = (size_t)1 << 20;
+  int mem_blocked = 0;                // graphs waiting for budget memory (guarded by mu)
   std::unordered_map<uint64_t, Query*> tickets;
   uint64_t next_ticket = 1;
   bool stop = false;
@@ -98,6 +109,8 @@ void fill_stats(const Query* q, bfs_query_stats* st) {
   st->status = q->status;
 }
 
+void complete(bfs_server* S, GraphEntry* ge);
+
 // Takes `bytes` of the budget; false if they do not fit.
 bool reserve(bfs_server* S, size_t bytes) {
   std::lock_guard<std::mutex> lk(S->mu);
@@ -106,11 +119,83 @@ bool reserve(bfs_server* S, size_t bytes) {
   return true;
 }
 
+void unreserve(bfs_server* S, size_t bytes) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->used -= bytes;
+}
+
+void set_blocked(bfs_server* S, GraphEntry* ge, bool blocked) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (ge->mem_blocked == blocked) return;
+  ge->mem_blocked = blocked;
+  S->mem_blocked += blocked ? 1 : -1;
+}
+
+// Another graph waits for budget memory that this one holds.
+bool others_blocked(bfs_server* S, GraphEntry* ge) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  return S->mem_blocked > (ge->mem_blocked ? 1 : 0);
+}
+
+void mark_done(bfs_server* S, Query* q, int status) {
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    q->status = status;
+    q->t_done = now_ns();
+    q->done = true;
+  }
+  S->cv_done.notify_all();
+}
+
+// Frees the group and the staging buffers (none may be in use) and returns
+// their bytes to the budget.
+void release_memory(bfs_server* S, GraphEntry* ge) {
+  if (ge->grp) {
+    gbfs::serve_group_destroy(ge->grp);
+    ge->grp = nullptr;
+    unreserve(S, ge->grp_bytes);
+    ge->grp_bytes = 0;
+  }
+  const size_t nbytes = sizeof(int32_t) * (size_t)ge->g->n;
+  for (int32_t* b : ge->staging_all) {
+    cudaFree(b);
+    unreserve(S, nbytes);
+  }
+  ge->staging_all.clear();
+  ge->staging_free.clear();
+}
+
+// A device-side failure of the group's launched levels: its running queries
+// end with that status, the group is freed (rebuilt by the next admission).
+// Only a CUDA error stays with the server.
+void fail_group(bfs_server* S, GraphEntry* ge, int rc) {
+  if (rc == BFS_ECUDA) S->error = rc;
+  for (int i = 0; i < 64; ++i) {
+    Query* q = ge->lane_q[i];
+    if (!q) continue;
+    ge->lane_q[i] = nullptr;
+    if (q->host_out) ge->staging_free.push_back(q->dev_out);
+    q->levels = 0;
+    mark_done(S, q, rc);
+  }
+  if (ge->grp) cudaStreamSynchronize(gbfs::serve_group_stream(ge->grp));
+  complete(S, ge);
+  if (ge->grp) {
+    gbfs::serve_group_destroy(ge->grp);
+    ge->grp = nullptr;
+    unreserve(S, ge->grp_bytes);
+    ge->grp_bytes = 0;
+  }
+}
+
 // The group's launched level is done: retire lanes whose frontier emptied.
 void finish_level(bfs_server* S, GraphEntry* ge) {
   unsigned long long retired = 0;
   const int rc = gbfs::serve_group_finish(ge->grp, &retired);
-  if (rc != BFS_OK) S->error = rc;
+  if (rc != BFS_OK) {
+    fail_group(S, ge, rc);
+    return;
+  }
   while (retired) {
     const int i = __builtin_ctzll(retired);
     retired &= retired - 1;
@@ -170,22 +255,42 @@ void admit(bfs_server* S, GraphEntry* ge) {
     const size_t nbytes = sizeof(int32_t) * (size_t)ge->g->n;
     if (!ge->grp) {
       const size_t need = gbfs::serve_group_bytes(ge->g, S->p.ms_ring);
-      if (!reserve(S, need)) break;
+      if (need + (q->host_out ? nbytes : 0) > S->budget) {
+        // This graph's group can never fit the budget: the query fails instead of waiting forever.
+        ge->waiting.pop_front();
+        {
+          std::lock_guard<std::mutex> lk(S->mu);
+          S->queued -= 1;
+        }
+        mark_done(S, q, BFS_ENOMEM);
+        --next_lane;
+        continue;
+      }
+      if (!reserve(S, need)) {
+        set_blocked(S, ge, true);  // other groups release memory once they drain
+        break;
+      }
       const int prio = ge->g->m < (long long)S->p.large_diameter_degree * ge->g->n ? 1 : 0;
       const int rc = gbfs::serve_group_create(ge->g, S->p.ms_ring, S->p.ms_heavy_min, prio, &ge->grp);
       if (rc != BFS_OK) {
+        unreserve(S, need);
         S->error = rc;
         break;
       }
+      ge->grp_bytes = need;
     }
     if (q->host_out) {
       if (ge->staging_free.empty()) {
-        if (!reserve(S, nbytes)) break;
+        if (!reserve(S, nbytes)) {
+          // No staging memory: wait for this group's running queries, or, with none running, for
+          // other groups to release theirs.
+          if (!gbfs::serve_group_lanes(ge->grp) && ge->completing.empty()) set_blocked(S, ge, true);
+          break;
+        }
         int32_t* buf = nullptr;
         if (cudaMalloc(&buf, nbytes) != cudaSuccess) {
           cudaGetLastError();
-          std::lock_guard<std::mutex> lk(S->mu);
-          S->used -= nbytes;
+          unreserve(S, nbytes);
           break;
         }
         ge->staging_free.push_back(buf);
@@ -197,6 +302,7 @@ void admit(bfs_server* S, GraphEntry* ge) {
       q->dev_out = q->user_out;
     }
     ge->waiting.pop_front();
+    set_blocked(S, ge, false);
     q->lane = lane;
     q->t_start = now_ns();
     q->join = gbfs::serve_group_lanes(ge->grp) ? gbfs::serve_group_level(ge->grp) : 0;
@@ -229,13 +335,18 @@ void graph_worker(bfs_server* S, GraphEntry* ge) {
     }
     if (ge->grp && gbfs::serve_group_ready(ge->grp) >= 0) finish_level(S, ge);  // blocks until the level is done
     complete(S, ge);
-    if (!stopping) admit(S, ge);
+    // While another graph waits for memory this one holds, admit nothing and
+    // release the memory once the running queries are done.
+    const bool yield = others_blocked(S, ge);
+    if (!stopping && !yield) admit(S, ge);
     const bool running = ge->grp && gbfs::serve_group_lanes(ge->grp);
     if (running) {
-      const int rc = gbfs::serve_group_launch(ge->grp, S->p.tau_inv);
-      if (rc != BFS_OK) S->error = rc;
+      const int rc = gbfs::serve_group_launch(ge->grp, S->p.tau_inv, (long long)S->p.timeout_ms * 1000000ll,
+                                              S->p.test_barrier_extra);
+      if (rc != BFS_OK) fail_group(S, ge, rc);
       continue;
     }
+    if (yield && ge->completing.empty() && (ge->grp || !ge->staging_all.empty())) release_memory(S, ge);
     if (!ge->completing.empty()) {
       std::this_thread::yield();
       continue;
@@ -257,10 +368,12 @@ int bfs_serve_create(size_t mem_budget, const bfs_params* params, bfs_server** o
   bfs_server* S = new bfs_server();
   S->budget = mem_budget;
   if (params) S->p = *params; else bfs_params_default(&S->p);
-  if (S->p.ms_ring < 2 || S->p.ms_ring > 16 || S->p.tau_inv < 1) {
+  if (S->p.ms_ring < 2 || S->p.ms_ring > 16 || S->p.tau_inv < 1 || S->p.timeout_ms < 1 ||
+      S->p.test_barrier_extra < 0 || S->p.serve_queue < 0) {
     delete S;
     return BFS_EINVAL;
   }
+  if (S->p.serve_queue > 0) S->queue_cap = (size_t)S->p.serve_queue;
   if (cudaGetDevice(&S->device) != cudaSuccess) {
     delete S;
     return BFS_ECUDA;
@@ -356,8 +469,7 @@ void bfs_serve_destroy(bfs_server* S) {
   // Queries never admitted (still queued at shutdown) and completed ones not yet
   // reported are all still registered under their tickets.
   for (GraphEntry* ge : ges) {
-    gbfs::serve_group_destroy(ge->grp);
-    for (int32_t* b : ge->staging_all) cudaFree(b);
+    release_memory(S, ge);
     delete ge;
   }
   for (auto& kv : S->tickets) delete kv.second;

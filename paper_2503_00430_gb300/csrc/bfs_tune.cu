@@ -1,11 +1,16 @@
-// Autotuner: picks bfs_params for a graph by coordinate descent.
+// Autotuner: picks bfs_params by coordinate descent, for single-source
+// queries (bfs_tune), multi-source calls and serving groups (bfs_tune_multi)
+// and graph sets (bfs_tune_graphset).
 //
 // The paper tunes by hand (static vs dynamic scheduling, Section 2; alpha and
 // beta of the edge-count rule it cites); here every candidate setting of one
-// parameter at a time is timed on sample sources (median of the per-source
-// CUDA-event times), the fastest is kept, and every candidate's distances must
-// hash identically to the starting setting's (the distances are unique, so a
-// parameter can only change speed - a mismatch is reported as an error).
+// parameter at a time is timed, the fastest is kept when it beats the current
+// setting by at least 2 %, and every candidate's output must hash identically
+// to the starting setting's (distances are unique, so a parameter can only
+// change speed - a mismatch is reported as an error).  A trial's time is the
+// best of three timed runs after a warm-up run (per source for single-source
+// queries, then the mean over the sources: the harmonic-mean rate over
+// sources of one component is ~ the reciprocal of their total time).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -24,59 +29,95 @@ __device__ __forceinline__ unsigned long long tmix(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
-// Order-independent hash of a distance array.
-__global__ void k_dist_hash(const int* d, long long n, unsigned long long* out) {
+// Order-independent hash of a distance array (int32 elements, or bytes when
+// `bytes` is set).
+__global__ void k_dist_hash(const void* d, long long n, int bytes, unsigned long long* out) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   unsigned long long h = 0;
-  for (long long v = tid; v < n; v += nth) h += tmix(((unsigned long long)v << 32) ^ (unsigned)d[v]);
+  for (long long v = tid; v < n; v += nth) {
+    const unsigned x = bytes ? (unsigned)static_cast<const unsigned char*>(d)[v] : (unsigned)static_cast<const int*>(d)[v];
+    h += tmix(((unsigned long long)v << 32) ^ x);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
   if ((threadIdx.x & 31u) == 0) atomicAdd(out, h);
 }
 
 struct Trial {
-  double median_ms = 0;
+  double ms = 0;            // objective: mean over sources (or one call) of the best timed run
   unsigned long long hash = 0;
   int rc = BFS_OK;
 };
 
-Trial run_trial(bfs_graph* g, const int* srcs, int k, const bfs_params& p, int* dist, unsigned long long* d_hash,
-                cudaStream_t s) {
-  Trial t;
-  std::vector<float> ms;
-  cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  unsigned long long hsum = 0;
-  for (int i = 0; i < k && t.rc == BFS_OK; ++i) {
-    for (int rep = 0; rep < 2 && t.rc == BFS_OK; ++rep) {  // first run warms the workspace and caches
-      cudaEventRecord(a, s);
-      t.rc = run_single(g, srcs[i], dist, p, nullptr, nullptr, 0, s);
-      cudaEventRecord(b, s);
-      cudaEventSynchronize(b);
-      if (rep == 1) {
-        float x = 0;
-        cudaEventElapsedTime(&x, a, b);
-        ms.push_back(x);
+// Times fn() three times after one warm-up run on stream s; the best run.
+template <typename F>
+int best_of_three(cudaStream_t s, cudaEvent_t a, cudaEvent_t b, F&& fn, float* out) {
+  float best = 0;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(a, s);
+    const int rc = fn();
+    cudaEventRecord(b, s);
+    if (rc != BFS_OK) return rc;
+    if (cudaEventSynchronize(b) != cudaSuccess) return BFS_ECUDA;
+    float x = 0;
+    cudaEventElapsedTime(&x, a, b);
+    if (rep == 1 || (rep > 1 && x < best)) best = x;
+  }
+  *out = best;
+  return BFS_OK;
+}
+
+unsigned long long hash_of(const void* d, long long n, int bytes, unsigned long long* d_hash, int grid,
+                           cudaStream_t s) {
+  cudaMemsetAsync(d_hash, 0, sizeof(unsigned long long), s);
+  k_dist_hash<<<grid, 256, 0, s>>>(d, n, bytes, d_hash);
+  unsigned long long h = 0;
+  cudaMemcpyAsync(&h, d_hash, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return h;
+}
+
+struct Field {
+  int32_t bfs_params::*f;
+  std::vector<int32_t> vals;
+};
+
+// Coordinate descent (two sweeps) from `cur`; `skip(cand, field)` drops
+// settings that cannot change the work.  Returns BFS_OK or the failing code.
+template <typename Eval, typename Skip>
+int descend(bfs_params& cur, const std::vector<Field>& fields, Eval&& eval, Skip&& skip, bfs_tune_report* report) {
+  Trial best = eval(cur);
+  if (best.rc != BFS_OK) return best.rc;
+  const unsigned long long ref_hash = best.hash;
+  const double start_ms = best.ms;
+  int trials = 1;
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    for (const Field& fd : fields) {
+      for (int32_t v : fd.vals) {
+        if (cur.*(fd.f) == v) continue;
+        bfs_params cand = cur;
+        cand.*(fd.f) = v;
+        if (skip(cand, fd.f)) continue;
+        Trial t = eval(cand);
+        ++trials;
+        if (t.rc == BFS_EINVAL || t.rc == BFS_ENOMEM) continue;  // a shape the device or budget does not allow
+        if (t.rc != BFS_OK) return t.rc;
+        if (t.hash != ref_hash) return BFS_ECUDA;  // a parameter changed the output: never expected
+        if (t.ms < best.ms * 0.98) {
+          best = t;
+          cur = cand;
+        }
       }
     }
-    if (t.rc != BFS_OK) break;
-    cudaMemsetAsync(d_hash, 0, sizeof(unsigned long long), s);
-    k_dist_hash<<<g->num_sms * 4, 256, 0, s>>>(dist, g->n, d_hash);
-    unsigned long long h = 0;
-    cudaMemcpyAsync(&h, d_hash, sizeof(h), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    hsum = hsum * 0x9E3779B97F4A7C15ull + h;
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  if (!ms.empty()) {
-    std::sort(ms.begin(), ms.end());
-    t.median_ms = ms[ms.size() / 2];
+  if (report) {
+    memset(report, 0, sizeof(*report));
+    report->trials = trials;
+    report->start_ms = start_ms;
+    report->best_ms = best.ms;
   }
-  t.hash = hsum;
-  return t;
+  return BFS_OK;
 }
 
 }  // namespace
@@ -95,75 +136,174 @@ extern "C" int bfs_tune(bfs_graph* g, const int32_t* srcs, int32_t k, const bfs_
   std::lock_guard<std::mutex> lock(g->mu);
   int rc = ensure_single_ws(g);
   if (rc != BFS_OK) return rc;
+  const bool small_world = (double)g->m >= 7.0 * (double)g->n;
+  if (small_world) rc = ensure_relabel_single(g);
+  if (rc != BFS_OK) return rc;
   int* dist = nullptr;
   unsigned long long* d_hash = nullptr;
   GBFS_CUDA(cudaMalloc(&dist, sizeof(int) * (size_t)g->n));
   GBFS_CUDA(cudaMalloc(&d_hash, sizeof(unsigned long long)));
   cudaStream_t s;
   GBFS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-  Trial best = run_trial(g, srcs, k, cur, dist, d_hash, s);
-  const unsigned long long ref_hash = best.hash;
-  const double start_ms = best.median_ms;
-  int trials = 1;
-  rc = best.rc;
-  // Coordinate descent over the tunable fields, two sweeps.
-  struct Field {
-    int32_t bfs_params::*f;
-    std::vector<int32_t> vals;
-  };
-  const bool small_world = (double)g->m >= 7.0 * (double)g->n;
-  std::vector<Field> fields = {
-      {&bfs_params::policy, {BFS_POLICY_EDGES, BFS_POLICY_FRONTIER, BFS_POLICY_TD_ONLY}},
-      {&bfs_params::alpha, {2, 4, 8, 14, 24, 48, 96}},
-      {&bfs_params::beta, {6, 12, 24, 48, 96}},
-      {&bfs_params::tau_inv, {5, 10, 20, 40, 80}},
-      {&bfs_params::chunk, {256, 512, 1024, 4096}},
-      {&bfs_params::small_max, {8, 16, 32}},
-      {&bfs_params::bu_thread_max, {0, 8, 32, 128}},
-      {&bfs_params::bu_warp_min, {8, 32, 128, 1024}},
-      {&bfs_params::bu_chunk, {0, 1, 4}},
-      {&bfs_params::threads_per_block, {256, 512, 1024}},
-  };
-  if (!small_world) fields.erase(fields.begin() + 1, fields.begin() + 4);  // top-down-only class: no switch rule
-  for (int sweep = 0; sweep < 2 && rc == BFS_OK; ++sweep) {
-    for (const Field& fd : fields) {
-      for (int32_t v : fd.vals) {
-        if (cur.*(fd.f) == v) continue;
-        bfs_params cand = cur;
-        cand.*(fd.f) = v;
-        // Only settings that can change the work of the current policy.
-        if (fd.f == &bfs_params::tau_inv && cand.policy != BFS_POLICY_FRONTIER) continue;
-        if ((fd.f == &bfs_params::alpha || fd.f == &bfs_params::beta) && cand.policy != BFS_POLICY_EDGES) continue;
-        Trial t = run_trial(g, srcs, k, cand, dist, d_hash, s);
-        ++trials;
-        if (t.rc != BFS_OK) {
-          if (t.rc == BFS_EINVAL) continue;  // e.g. an occupancy the block shape does not allow
-          rc = t.rc;
-          break;
-        }
-        if (t.hash != ref_hash) {
-          rc = BFS_ECUDA;  // a parameter changed the distances: never expected
-          break;
-        }
-        if (t.median_ms < best.median_ms * 0.98) {
-          best = t;
-          cur = cand;
-        }
-      }
-      if (rc != BFS_OK) break;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  auto eval = [&](const bfs_params& p) {
+    Trial t;
+    double sum = 0;
+    for (int i = 0; i < k && t.rc == BFS_OK; ++i) {
+      float ms = 0;
+      t.rc = best_of_three(s, a, b, [&] { return run_single(g, srcs[i], dist, p, nullptr, nullptr, 0, s); }, &ms);
+      if (t.rc != BFS_OK) break;
+      sum += ms;
+      t.hash = t.hash * 0x9E3779B97F4A7C15ull + hash_of(dist, g->n, 0, d_hash, g->num_sms * 4, s);
     }
+    t.ms = sum / k;
+    return t;
+  };
+  std::vector<Field> fields;
+  if (small_world) {
+    fields = {
+        {&bfs_params::policy, {BFS_POLICY_EDGES, BFS_POLICY_FRONTIER}},
+        {&bfs_params::alpha, {2, 4, 8, 14, 24, 48, 96}},
+        {&bfs_params::beta, {6, 12, 24, 48, 96}},
+        {&bfs_params::tau_inv, {5, 10, 20, 40, 80}},
+        {&bfs_params::relabel, {0, 1}},
+        {&bfs_params::chunk, {256, 512, 1024, 4096}},
+        {&bfs_params::small_max, {8, 16, 32}},
+        {&bfs_params::bu_thread_max, {0, 8, 32, 128}},
+        {&bfs_params::bu_warp_min, {8, 32, 128, 1024}},
+        {&bfs_params::bu_chunk, {0, 1, 4}},
+        {&bfs_params::threads_per_block, {256, 512, 1024}},
+        {&bfs_params::blocks_per_sm, {0, 1}},
+    };
+  } else {  // Section 3's large-diameter class: top-down only, level-synchronous or several levels per barrier
+    fields = {
+        {&bfs_params::policy, {BFS_POLICY_TD_ONLY, BFS_POLICY_LOCAL}},
+        {&bfs_params::local_levels, {4, 8, 16, 32, 64}},
+        {&bfs_params::local_threads, {64, 128, 256}},
+        {&bfs_params::chunk, {256, 1024}},
+        {&bfs_params::threads_per_block, {256, 512, 1024}},
+        {&bfs_params::blocks_per_sm, {0, 1, 2, 4}},
+    };
   }
+  const int policy0 = cur.policy;
+  auto skip = [&](const bfs_params& c, int32_t bfs_params::*f) {
+    const int pol = c.policy == BFS_POLICY_AUTO ? policy0 : c.policy;
+    const bool local = pol == BFS_POLICY_LOCAL || (pol == BFS_POLICY_AUTO && !small_world);
+    if (f == &bfs_params::tau_inv) return pol != BFS_POLICY_FRONTIER;
+    if (f == &bfs_params::alpha || f == &bfs_params::beta) return pol != BFS_POLICY_EDGES && pol != BFS_POLICY_AUTO;
+    if (f == &bfs_params::local_levels || f == &bfs_params::local_threads) return !local;
+    if (f == &bfs_params::chunk || f == &bfs_params::threads_per_block) return local;
+    return false;
+  };
+  rc = descend(cur, fields, eval, skip, report);
+  if (report) report->sources = k;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
   cudaStreamDestroy(s);
   cudaFree(dist);
   cudaFree(d_hash);
   if (rc != BFS_OK) return rc;
   *out = cur;
-  if (report) {
-    memset(report, 0, sizeof(*report));
-    report->trials = trials;
-    report->start_ms = start_ms;
-    report->best_ms = best.median_ms;
-    report->sources = k;
-  }
+  return BFS_OK;
+}
+
+extern "C" int bfs_tune_multi(bfs_graph* g, const int32_t* srcs, int32_t k, int dist_bits, const bfs_params* base,
+                              bfs_params* out, bfs_tune_report* report) {
+  if (!g || !srcs || k <= 0 || !out || (dist_bits != 8 && dist_bits != 32)) return BFS_EINVAL;
+  for (int i = 0; i < k; ++i)
+    if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return BFS_EINVAL;
+  bfs_params cur;
+  if (base) cur = *base; else bfs_params_default(&cur);
+  const size_t esz = (size_t)dist_bits / 8;
+  void* dist = nullptr;
+  unsigned long long* d_hash = nullptr;
+  GBFS_CUDA(cudaMalloc(&dist, esz * (size_t)k * (size_t)g->n));
+  GBFS_CUDA(cudaMalloc(&d_hash, sizeof(unsigned long long)));
+  cudaStream_t s;
+  GBFS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  auto eval = [&](const bfs_params& p) {
+    Trial t;
+    float ms = 0;
+    {
+      std::lock_guard<std::mutex> lock(g->mu);
+      t.rc = best_of_three(s, a, b, [&] { return run_multi(g, srcs, k, dist, dist_bits, p, nullptr, s); }, &ms);
+    }
+    if (t.rc == BFS_OK)
+      t.hash = hash_of(dist, (long long)k * g->n, dist_bits == 8, d_hash, g->num_sms * 8, s);
+    t.ms = ms;
+    return t;
+  };
+  const std::vector<Field> fields = {
+      {&bfs_params::ms_alpha, {1, 2, 4, 8, 16}},
+      {&bfs_params::ms_heavy_min, {64, 256, 1024}},
+      {&bfs_params::ms_ring, {4, 8, 16}},
+      {&bfs_params::ms_lanes, {64, 128, 256}},
+      {&bfs_params::ms_relabel, {0, 1}},
+      {&bfs_params::ms_degree_order, {0, 1}},
+  };
+  auto skip = [&](const bfs_params& c, int32_t bfs_params::*f) {
+    if (f == &bfs_params::ms_lanes) return c.ms_lanes > k;
+    if (f == &bfs_params::ms_degree_order) return c.ms_relabel != 0;  // the renumbered copy is in degree order
+    return false;
+  };
+  const int rc = descend(cur, fields, eval, skip, report);
+  if (report) report->sources = k;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaStreamDestroy(s);
+  cudaFree(dist);
+  cudaFree(d_hash);
+  if (rc != BFS_OK) return rc;
+  *out = cur;
+  return BFS_OK;
+}
+
+extern "C" int bfs_tune_graphset(bfs_graphset* set, const int32_t* srcs, const bfs_params* base, bfs_params* out,
+                                 bfs_tune_report* report) {
+  if (!set || !srcs || !out) return BFS_EINVAL;
+  bfs_params cur;
+  if (base) cur = *base; else bfs_params_default(&cur);
+  if (cur.threads_per_block > 512) cur.threads_per_block = 512;
+  const long long total = graphset_total_vertices(set);
+  int* dist = nullptr;
+  unsigned long long* d_hash = nullptr;
+  GBFS_CUDA(cudaMalloc(&dist, sizeof(int) * (size_t)total));
+  GBFS_CUDA(cudaMalloc(&d_hash, sizeof(unsigned long long)));
+  cudaStream_t s;
+  GBFS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto eval = [&](const bfs_params& p) {
+    Trial t;
+    float ms = 0;
+    t.rc = best_of_three(s, a, b, [&] { return bfs_graphset_run(set, srcs, dist, &p, nullptr, s); }, &ms);
+    if (t.rc == BFS_OK) t.hash = hash_of(dist, total, 0, d_hash, sms * 4, s);
+    t.ms = ms;
+    return t;
+  };
+  const std::vector<Field> fields = {
+      {&bfs_params::threads_per_block, {128, 256, 512}},
+      {&bfs_params::blocks_per_sm, {0, 1, 2, 4, 8}},
+      {&bfs_params::alpha, {4, 14, 48}},
+      {&bfs_params::beta, {12, 24, 96}},
+  };
+  const int rc = descend(cur, fields, eval, [](const bfs_params&, int32_t bfs_params::*) { return false; }, report);
+  if (report) report->sources = graphset_count(set);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaStreamDestroy(s);
+  cudaFree(dist);
+  cudaFree(d_hash);
+  if (rc != BFS_OK) return rc;
+  *out = cur;
   return BFS_OK;
 }

@@ -50,9 +50,9 @@ def check_single_source_workload(bfs, argv):
     rp, col, srcs, _, _ = bench.make_workload(args)
     assert len(srcs) == bench.NSRC == 64
     g = bfs.bfs_graph_upload(rp, col, flags=bench.upload_flags(bfs, args))
-    params = bench.query_params(bfs, args)
-    stream = torch.cuda.Stream()
     n = len(rp) - 1
+    params = bench.query_params(bfs, args, n, len(col))
+    stream = torch.cuda.Stream()
     d = torch.empty(n, dtype=torch.int32, device="cuda")
     host = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
     checked = 0
@@ -72,10 +72,10 @@ def check_single_source_workload(bfs, argv):
 
 
 def test_rmat_s25_bench_configuration_all_64_sources(bfs):
-    """The headline: R-MAT scale 25, int64 row pointers, degree-ordered lists, queries on the
-    degree-renumbered copy, one persistent launch per BFS."""
+    """The headline: R-MAT scale 25, int64 row pointers, degree-ordered lists, the bench's query
+    parameters (the tuning table's entry for the graph's class)."""
     args = bench.parse_args([])
-    assert args.workload == "rmat25" and args.relabel == 1 and args.launch == 0 and args.policy == 0
+    assert args.workload == "rmat25" and args.policy is None and args.launch is None and args.relabel is None
     check_single_source_workload(bfs, [])
 
 
@@ -107,8 +107,9 @@ def test_msbfs_rmat_s24_all_256_rows(bfs):
     rp, col, srcs = bench.msbfs_workload()
     n = len(rp) - 1
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | bfs.BFS_DEGREE_ORDER)
+    mp = bfs.tuned_params(None, g, "multi")
     out = torch.empty((256, n), dtype=torch.uint8, device="cuda")
-    bfs.bfs_multi(g, srcs, out, dist_bits=8)
+    bfs.bfs_multi_ex(g, srcs, out, dist_bits=8, params=mp)
     torch.cuda.synchronize()
     sample32 = set(range(0, 256, 17)) | {255}
     want32 = {}
@@ -122,7 +123,7 @@ def test_msbfs_rmat_s24_all_256_rows(bfs):
         del want, got
     del out
     out32 = torch.empty((256, n), dtype=torch.int32, device="cuda")
-    bfs.bfs_multi(g, srcs, out32, dist_bits=32)
+    bfs.bfs_multi_ex(g, srcs, out32, dist_bits=32, params=mp)
     for i, w in want32.items():
         assert np.array_equal(out32[i].cpu().numpy(), w), i
     del out32
@@ -174,7 +175,7 @@ def test_graphset_10000_every_graph(bfs):
     gs = graphgen.graph_set(10000, 1000, 100000, 8.0, seed=4)
     s = bfs.bfs_graphset_upload(gs.voff, gs.eoff, gs.row_ptr, gs.col)
     dist = torch.empty(int(gs.voff[-1]), dtype=torch.int32, device="cuda")
-    bfs.bfs_graphset_run(s, gs.src, dist)
+    bfs.bfs_graphset_run(s, gs.src, dist, params=bfs.tuned_params(None, None, "graphset"))
     got = dist.cpu().numpy()
 
     def ok(i):
