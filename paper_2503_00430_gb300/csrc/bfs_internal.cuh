@@ -83,10 +83,8 @@ struct KParams {
   // Degree-renumbered graph (single-source queries with params->relabel): the
   // search runs in new ids; dist is written in the caller's ids through these
   // maps.  Null: the graph as uploaded.
-  const int* new_of = nullptr;   // [n] caller id -> new id
-  const int* old_of = nullptr;   // [n] new id -> caller id: level bytes and distances are written at
-                                 // the caller's id of a found vertex
-  int src_out = 0;               // the source's caller id (= src on the graph as uploaded)
+  const int* new_of = nullptr;   // [n] caller id -> new id (expansion of the level bytes)
+  const int* old_of = nullptr;   // [n] new id -> caller id (direct int32 writes past level 254)
 };
 
 // Direction of level `next_level` (true = top-down), from the counters of the

@@ -137,7 +137,6 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   K.m = m;
   K.nw = (int)((n + 31) / 32);
   K.src = src;
-  K.src_out = src;
   K.init_vis = reinterpret_cast<unsigned*>(b + lay.init_vis);
   K.head = nullptr;
   K.lv8 = nullptr;

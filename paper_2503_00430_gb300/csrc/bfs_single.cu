@@ -35,21 +35,11 @@ namespace {
 using namespace dev;
 
 
-// The level of a found vertex is L + 1: a level byte while the search keeps
-// them (direct = false), else its int32 distance; both are indexed by the
-// caller's id `vo`, so the final expansion is a sequential pass.
-__device__ __forceinline__ void mark_level(const KParams& P, bool direct, int vo, int L) {
-  if (direct) P.dist[vo] = L + 1;
-  else st_u8_last(P.lv8 + vo, (unsigned)(L + 1));
-}
-
-// Caller id of search vertex v (its own id unless the search runs on the renumbered copy).
-__device__ __forceinline__ int caller_id(const KParams& P, int v) { return P.old_of ? __ldg(P.old_of + v) : v; }
-
-// Asynchronous 4-byte global -> shared copy (zero-filled when src_bytes is 0).
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+// The level of vertex v is L + 1: a level byte while the search keeps them
+// (direct = false), else its int32 distance.
+__device__ __forceinline__ void mark_level(const KParams& P, bool direct, int v, int L) {
+  if (direct) P.dist[P.old_of ? P.old_of[v] : v] = L + 1;
+  else st_u8_last(P.lv8 + v, (unsigned)(L + 1));
 }
 
 __device__ __forceinline__ unsigned long long pack_item(long long start, int len) {
@@ -123,7 +113,7 @@ __device__ __noinline__ void init_phase(const KParams& P) {
     const long long n16 = (n + 15) >> 4;
     for (long long i = tid; i < n16; i += nth) {
       unsigned w[4] = {kFull, kFull, kFull, kFull};
-      if ((long long)(P.src_out >> 4) == i) w[(P.src_out >> 2) & 3] &= ~(0xffu << (8 * (P.src_out & 3)));
+      if ((long long)(P.src >> 4) == i) w[(P.src >> 2) & 3] &= ~(0xffu << (8 * (P.src & 3)));
       st_v4_last(P.lv8 + 16 * i, w[0], w[1], w[2], w[3]);
     }
   } else if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
@@ -131,8 +121,8 @@ __device__ __noinline__ void init_phase(const KParams& P) {
     const long long n4 = n >> 2;
     for (long long i = tid; i < n4; i += nth) {
       int4 v = make_int4(-1, -1, -1, -1);
-      if ((long long)(P.src_out >> 2) == i) {
-        int k = P.src_out & 3;
+      if ((long long)(P.src >> 2) == i) {
+        int k = P.src & 3;
         if (k == 0) v.x = 0;
         if (k == 1) v.y = 0;
         if (k == 2) v.z = 0;
@@ -140,9 +130,9 @@ __device__ __noinline__ void init_phase(const KParams& P) {
       }
       d4[i] = v;
     }
-    for (long long i = (n4 << 2) + tid; i < n; i += nth) P.dist[i] = (i == P.src_out) ? 0 : -1;
+    for (long long i = (n4 << 2) + tid; i < n; i += nth) P.dist[i] = (i == P.src) ? 0 : -1;
   } else {
-    for (long long i = tid; i < n; i += nth) P.dist[i] = (i == P.src_out) ? 0 : -1;
+    for (long long i = tid; i < n; i += nth) P.dist[i] = (i == P.src) ? 0 : -1;
   }
   const int sw = P.src >> 5;
   for (long long w = tid; w < P.nw; w += nth) {
@@ -152,13 +142,33 @@ __device__ __noinline__ void init_phase(const KParams& P) {
   }
 }
 
-// dist[v] = level byte of v, or -1 where it is 255 (every vertex written; the
-// bytes are indexed by caller id, so this is one sequential pass).
+// dist[v] = level byte of v, or -1 where it is 255 (every vertex written).
+// On a renumbered graph the byte of caller vertex v is at new_of[v]; a
+// vertex of degree 0 (new id >= n_live) other than the source is unreached.
 __device__ __noinline__ void expand_phase(const KParams& P) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long n = P.n;
   long long done = 0;
+  if (P.new_of) {
+    auto level_of = [&](int nv) -> int {
+      if ((long long)nv >= P.n_live && nv != P.src) return -1;
+      const int t = P.lv8[nv];
+      return t == 255 ? -1 : t;
+    };
+    if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
+      const long long n4 = n >> 2;
+      const int4* m4 = reinterpret_cast<const int4*>(P.new_of);
+      int4* d4 = reinterpret_cast<int4*>(P.dist);
+      for (long long i = tid; i < n4; i += nth) {
+        const int4 a = __ldcs(m4 + i);
+        __stcs(d4 + i, make_int4(level_of(a.x), level_of(a.y), level_of(a.z), level_of(a.w)));
+      }
+      done = n4 << 2;
+    }
+    for (long long i = done + tid; i < n; i += nth) P.dist[i] = level_of(P.new_of[i]);
+    return;
+  }
   if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
     const long long n4 = n >> 2;
     const unsigned* l4 = reinterpret_cast<const unsigned*>(P.lv8);
@@ -270,14 +280,13 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, bool direct, 
     if (!(old[k] & (1u << (c[k] & 31)))) cl |= 1u << k;
   if (__ballot_sync(kFull, cl != 0) == 0) return;
   long long s[4];
-  int d[4], vo[4];
+  int d[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     s[k] = 0;
     d[k] = 0;
-    vo[k] = c[k];
     if ((cl >> k) & 1u) {
-      vo[k] = caller_id(P, c[k]);  // requested together with the head record
+      mark_level(P, direct, c[k], L);
       if (P.head) {
         const int4 h = __ldg(P.head + c[k]);
         s[k] = h.z;
@@ -288,9 +297,6 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, bool direct, 
       }
     }
   }
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if ((cl >> k) & 1u) mark_level(P, direct, vo[k], L);
   const int ncl = __popc(cl);
   int nsm = 0, nlg = 0;
   unsigned long long dsum = 0;
@@ -452,21 +458,19 @@ constexpr int kNBuf = kDepth + 1;
 struct BuWarpSmem {
   int4 hbuf[kNBuf][32 * kBuU];   // head records of the rounds in flight (lane-private slots)
   int vbuf[kNBuf][32 * kBuU];    // their vertices
-  int obuf[kNBuf][32 * kBuU];    // their caller ids (renumbered copy only)
   unsigned next[32];             // new-frontier bits of the batch's 32 words
   long long pstart[kPendCap];    // deferred scan: next entry to examine
   int plen[kPendCap];            // entries left
   int pv[kPendCap];              // vertex
-  int pvo[kPendCap];             // its caller id
   int pd[kPendCap];              // its degree
   int pex[kPendCap];             // entries examined so far (statistics)
   int npend;
 };
 
-__device__ __forceinline__ void bu_mark_found(const KParams& P, int L, bool direct, BuWarpSmem& sm, long long w0, int v,
-                                              int vo, int d, Acc& acc) {
+__device__ __forceinline__ void bu_mark_found(const KParams& P, int L, bool direct, BuWarpSmem& sm, long long w0, int v, int d,
+                                              Acc& acc) {
   atomicOr(&sm.next[(int)((long long)v / 32 - w0)], 1u << (v & 31));
-  mark_level(P, direct, vo, L);
+  mark_level(P, direct, v, L);
   acc.found += 1;
   acc.mf += (unsigned long long)d;
 }
@@ -487,7 +491,6 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
     long long ps = have ? sm.pstart[j] : 0;
     int pl = have ? sm.plen[j] : 0;
     const int pv = have ? sm.pv[j] : 0;
-    const int pvo = have ? sm.pvo[j] : 0;
     const int pdeg = have ? sm.pd[j] : 0;
     int ex = have ? sm.pex[j] : 0;
     // Each lane first continues its own vertex for up to bu_thread_max entries,
@@ -605,7 +608,7 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
         ex += (int)hx;
       }
     }
-    if (found) bu_mark_found(P, L, direct, sm, w0, pv, pvo, pdeg, acc);
+    if (found) bu_mark_found(P, L, direct, sm, w0, pv, pdeg, acc);
     if (STATS && have) acc.edges += (unsigned long long)ex;
   }
   __syncwarp();
@@ -641,7 +644,6 @@ __device__ __forceinline__ void bu_issue_round(const KParams& P, BuWarpSmem& sm,
   for (int k = 0; k < kBuU; ++k) {
     sm.vbuf[b][32 * k + lane] = v[k];
     cp_async16_first(&sm.hbuf[b][32 * k + lane], v[k] >= 0 ? P.head + v[k] : P.head, v[k] >= 0 ? 16 : 0);
-    if (P.old_of) cp_async4(&sm.obuf[b][32 * k + lane], v[k] >= 0 ? P.old_of + v[k] : P.old_of, v[k] >= 0 ? 4 : 0);
   }
 }
 
@@ -713,12 +715,8 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
         bu_probe_words(sm, front, (r + 1) % kNBuf, nw0, nw1);
       }
       const int buf = r % kNBuf;
-      int vo[kBuU];
 #pragma unroll
-      for (int k = 0; k < kBuU; ++k) {
-        v[k] = sm.vbuf[buf][32 * k + lane];
-        vo[k] = P.old_of ? sm.obuf[buf][32 * k + lane] : v[k];
-      }
+      for (int k = 0; k < kBuU; ++k) v[k] = sm.vbuf[buf][32 * k + lane];
       int4 hd[kBuU];
 #pragma unroll
       for (int k = 0; k < kBuU; ++k) hd[k] = v[k] >= 0 ? sm.hbuf[buf][32 * k + lane] : make_int4(-1, -1, 0, 0);
@@ -735,14 +733,13 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
         if (v[k] < 0) continue;
         const int d = hd[k].w;
         if (f0[k] | f1[k]) {
-          bu_mark_found(P, L, direct, sm, w0, v[k], vo[k], d, acc);
+          bu_mark_found(P, L, direct, sm, w0, v[k], d, acc);
           if (STATS) acc.edges += f0[k] ? 1ull : 2ull;
         } else if (d > 2) {
           const int slot = atomicAdd(&sm.npend, 1);
           sm.pstart[slot] = (long long)hd[k].z + 2;
           sm.plen[slot] = d - 2;
           sm.pv[slot] = v[k];
-          sm.pvo[slot] = vo[k];
           sm.pd[slot] = d;
           sm.pex[slot] = 2;
         } else if (STATS) {
@@ -789,14 +786,13 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
         const int d = (int)(e[k] - s[k]);
         const long long rest = a0 + 4;
         if (hit >= 0) {
-          bu_mark_found(P, L, direct, sm, w0, v[k], caller_id(P, v[k]), d, acc);
+          bu_mark_found(P, L, direct, sm, w0, v[k], d, acc);
           if (STATS) acc.edges += (unsigned long long)(hit - s[k] + 1);
         } else if (rest < e[k]) {
           const int slot = atomicAdd(&sm.npend, 1);
           sm.pstart[slot] = rest;
           sm.plen[slot] = (int)(e[k] - rest);
           sm.pv[slot] = v[k];
-          sm.pvo[slot] = caller_id(P, v[k]);
           sm.pd[slot] = d;
           sm.pex[slot] = (int)(rest - s[k]);
         } else if (STATS) {
@@ -1235,7 +1231,6 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
   K.m = g->m;
   K.nw = g->nw;
   K.src = rl ? rl->h_new_of[src] : src;
-  K.src_out = src;
   K.init_vis = rl ? rl->init_vis : g->init_vis;
   K.head = rl ? rl->head : g->head;
   K.new_of = rl ? rl->new_of : nullptr;
