@@ -235,6 +235,21 @@ const char *bfs_strerror(int code);
 /* Library version, major*10000 + minor*100 + patch. */
 int bfs_version(void);
 
+/*
+ * Bounds-checked builds (compiled with -DGBFS_DEBUG_BOUNDS; the library's
+ * stand-in for a device memory checker): every data-dependent global index of
+ * the single-source kernels (level-synchronous and BFS_POLICY_LOCAL) is
+ * checked against its array; the first out-of-range index is recorded and the
+ * access is redirected to element 0, so the kernel completes.
+ *  first_violation  0 if none, else bit 63 set | site << 48 | the low 48 bits
+ *                   of the index (site numbers name the access in the source).
+ *  checked          NULL or set to 1 when this library was built with the
+ *                   checks (0: release build, first_violation is always 0).
+ *  reset            nonzero clears the recorded violation.
+ * Errors: BFS_EINVAL (null first_violation), BFS_ECUDA.
+ */
+int bfs_debug_bounds(uint64_t *first_violation, int *checked, int reset);
+
 /* Fill *p with the defaults listed in bfs_params. */
 void bfs_params_default(bfs_params *p);
 

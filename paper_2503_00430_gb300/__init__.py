@@ -164,6 +164,7 @@ _vp, _i32, _i64, _u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.
 _SIGNATURES = [
     ("bfs_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("bfs_version", ctypes.c_int, []),
+    ("bfs_debug_bounds", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("bfs_params_default", None, [ctypes.POINTER(bfs_params)]),
     ("bfs_graph_upload", ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
     ("bfs_graph_free", None, [_vp]),
@@ -252,6 +253,14 @@ def bfs_strerror(code: int) -> str:
 
 def bfs_version() -> int:
     return int(load().bfs_version())
+
+
+def bfs_debug_bounds(reset: bool = False) -> tuple[int, bool]:
+    """(first recorded out-of-range index word or 0, whether this library checks bounds)."""
+    v = ctypes.c_uint64()
+    c = ctypes.c_int()
+    _check(load().bfs_debug_bounds(ctypes.byref(v), ctypes.byref(c), 1 if reset else 0), "bfs_debug_bounds")
+    return v.value, bool(c.value)
 
 
 def bfs_params_default() -> bfs_params:

@@ -329,6 +329,16 @@ const char* bfs_strerror(int code) {
 
 int bfs_version(void) { return 10000; }
 
+int bfs_debug_bounds(uint64_t* first_violation, int* checked, int reset) {
+  if (!first_violation) return BFS_EINVAL;
+  unsigned long long a = 0, b = 0;
+  const bool ca = bounds_read_single(&a, reset != 0);
+  const bool cb = bounds_read_local(&b, reset != 0);
+  if (checked) *checked = (ca || cb) ? 1 : 0;
+  *first_violation = a ? a : b;
+  return cudaGetLastError() == cudaSuccess ? BFS_OK : BFS_ECUDA;
+}
+
 void bfs_params_default(bfs_params* p) {
   if (!p) return;
   memset(p, 0, sizeof(*p));
@@ -360,6 +370,7 @@ void bfs_params_default(bfs_params* p) {
 
 int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n, int64_t m,
                      int flags, bfs_graph** out) {
+  GBFS_NVTX("bfs_graph_upload");
   if (!out) return BFS_EINVAL;
   *out = nullptr;
   if (!row_ptr || (m > 0 && !col_idx)) return BFS_EINVAL;
@@ -406,6 +417,7 @@ int bfs_graph_upload(const void* row_ptr, int row_ptr_bits, const int32_t* col_i
 }
 
 void bfs_graph_free(bfs_graph* g) {
+  GBFS_NVTX("bfs_graph_free");
   if (!g) return;
   cudaDeviceSynchronize();
   release_graph(g);
@@ -422,6 +434,7 @@ int bfs_graph_info(const bfs_graph* g, int64_t* n, int64_t* m, int64_t* max_degr
 
 int bfs_single_ex(bfs_graph* g, int32_t src, int32_t* dist, const bfs_params* params, bfs_stats* stats,
                   bfs_level_stat* levels, int32_t level_cap, void* stream) {
+  GBFS_NVTX("bfs_single_ex");
   if (!g || !dist) return BFS_EINVAL;
   if (src < 0 || (int64_t)src >= g->n) return BFS_EINVAL;
   if (level_cap < 0 || (level_cap > 0 && !levels)) return BFS_EINVAL;
@@ -458,6 +471,7 @@ int bfs_single(bfs_graph* g, int32_t src, int32_t* dist, void* stream) {
 
 int bfs_multi_ex(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int dist_bits, const bfs_params* params,
                  bfs_multi_stats* stats, void* stream) {
+  GBFS_NVTX("bfs_multi_ex");
   if (!g || !srcs || !dist || k <= 0) return BFS_EINVAL;
   if (dist_bits != 8 && dist_bits != 32) return BFS_EINVAL;
   for (int32_t i = 0; i < k; ++i)
@@ -476,6 +490,7 @@ int bfs_multi_ex(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int d
 }
 
 int bfs_parents(bfs_graph* g, const int32_t* dist, int32_t* parent, void* stream) {
+  GBFS_NVTX("bfs_parents");
   if (!g || !dist || !parent) return BFS_EINVAL;
   if (!is_device_pointer(dist) || !is_device_pointer(parent)) return BFS_EINVAL;
   std::lock_guard<std::mutex> lock(g->mu);
@@ -484,6 +499,7 @@ int bfs_parents(bfs_graph* g, const int32_t* dist, int32_t* parent, void* stream
 
 int bfs_single_nonatomic(bfs_graph* g, int32_t src, int32_t* dist, bfs_dup_stats* stats, bfs_dup_level* levels,
                          int32_t level_cap, void* stream) {
+  GBFS_NVTX("bfs_single_nonatomic");
   if (!g || !dist) return BFS_EINVAL;
   if (src < 0 || (int64_t)src >= g->n) return BFS_EINVAL;
   if (level_cap < 0 || (level_cap > 0 && !levels)) return BFS_EINVAL;

@@ -212,6 +212,7 @@ extern "C" {
 
 int bfs_graphset_upload(const int64_t* voff, const int64_t* eoff, const int64_t* row_ptr, const int32_t* col,
                         int32_t count, int flags, bfs_graphset** out) {
+  GBFS_NVTX("bfs_graphset_upload");
   if (!out) return BFS_EINVAL;
   *out = nullptr;
   if (!voff || !eoff || !row_ptr || count < 1) return BFS_EINVAL;
@@ -296,6 +297,7 @@ void bfs_graphset_free(bfs_graphset* s) {
 
 int bfs_graphset_run(bfs_graphset* s, const int32_t* srcs, int32_t* dist, const bfs_params* params,
                      bfs_graphset_stats* stats, void* stream) {
+  GBFS_NVTX("bfs_graphset_run");
   if (!s || !srcs || !dist) return BFS_EINVAL;
   bfs_params p;
   if (params) p = *params; else bfs_params_default(&p);

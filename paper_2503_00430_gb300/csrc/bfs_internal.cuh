@@ -6,9 +6,21 @@
 
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bfs.h"
 
 namespace gbfs {
+
+// An NVTX range around one API call, so profiler timelines name the library's
+// work (a no-op unless a profiling tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define GBFS_NVTX(name) ::gbfs::NvtxRange gbfs_nvtx_range_(name)
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -85,6 +97,8 @@ struct KParams {
   // maps.  Null: the graph as uploaded.
   const int* new_of = nullptr;   // [n] caller id -> new id (expansion of the level bytes)
   const int* old_of = nullptr;   // [n] new id -> caller id (direct int32 writes past level 254)
+  long long col_cap = 0;         // readable entries of col (bounds-checked build)
+  long long mg_cap = 0;          // entries of mg0 / mg1 (bounds-checked build)
 };
 
 // Direction of level `next_level` (true = top-down), from the counters of the
@@ -225,6 +239,11 @@ int serve_group_join(ServeGroup* G, int count, const int* lanes_idx, const int* 
 int serve_group_launch(ServeGroup* G, int tau_inv, long long timeout_ns, int barrier_extra);
 int serve_group_ready(ServeGroup* G);
 int serve_group_finish(ServeGroup* G, unsigned long long* retired);
+// Bounds-checked build (GBFS_DEBUG_BOUNDS): first recorded violation of each
+// kernel file (bit 63 set, site << 48 | low 48 bits of the index; 0 = none),
+// optionally cleared.  Both return false when the file was built without checks.
+bool bounds_read_single(unsigned long long* first, bool reset);
+bool bounds_read_local(unsigned long long* first, bool reset);
 // Graph-set facts for the tuner (bfs_graphset.cu).
 long long graphset_total_vertices(const bfs_graphset* s);
 int graphset_count(const bfs_graphset* s);

@@ -42,6 +42,21 @@ namespace {
 
 using namespace dev;
 
+// Bounds-checked build: as in bfs_single.cu, each data-dependent global index
+// is checked and the first violation recorded (the access goes to element 0).
+#ifdef GBFS_DEBUG_BOUNDS
+__device__ unsigned long long g_local_bounds_err;
+__device__ __forceinline__ long long lchk(long long i, long long lim, int site) {
+  if (i >= 0 && i < lim) return i;
+  atomicCAS(&g_local_bounds_err, 0ull,
+            (1ull << 63) | ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+  return 0;
+}
+#define LCHK(i, lim, site) lchk((long long)(i), (long long)(lim), (site))
+#else
+#define LCHK(i, lim, site) (i)
+#endif
+
 constexpr unsigned kInf = 0xffffffffu;
 constexpr int kLocalWindow = 1 << 20;  // row entries per lane per pass of a warp group
 constexpr int kLocalThreads = 512;     // largest block of the local kernel
@@ -81,14 +96,14 @@ struct LParams {
 template <typename RP>
 __device__ __forceinline__ void row_of(const LParams& P, int v, long long& start, int& deg, int& n0, int& n1) {
   if (P.head) {
-    const int4 h = __ldg(P.head + v);
+    const int4 h = __ldg(P.head + LCHK(v, P.n, 101));
     n0 = h.x;
     n1 = h.y;
     start = h.z;
     deg = h.w;
   } else {
-    start = rp_at<RP>(P.rp, v);
-    deg = (int)(rp_at<RP>(P.rp, (long long)v + 1) - start);
+    start = rp_at<RP>(P.rp, LCHK(v, P.n + 1, 102));
+    deg = (int)(rp_at<RP>(P.rp, LCHK((long long)v + 1, P.n + 1, 103)) - start);
     n0 = n1 = -1;
   }
 }
@@ -108,7 +123,7 @@ __device__ __forceinline__ void append_global(const LParams& P, int s, const int
   for (int k = 0; k < 4; ++k)
     if ((imp >> k) & 1u) {
       const unsigned bit = 1u << (v[k] & 31);
-      if (!(atomicOr(qbn + (v[k] >> 5), bit) & bit)) take |= 1u << k;
+      if (!(atomicOr(qbn + LCHK(v[k] >> 5, P.nw, 104), bit) & bit)) take |= 1u << k;
     }
   const int cnt = __popc(take);
   if (__ballot_sync(kFull, cnt != 0) == 0) return;
@@ -119,7 +134,7 @@ __device__ __forceinline__ void append_global(const LParams& P, int s, const int
   b = __shfl_sync(kFull, b, 31) + (unsigned long long)(incl - cnt);
 #pragma unroll
   for (int k = 0; k < 4; ++k)
-    if ((take >> k) & 1u) qn[b++] = v[k];
+    if ((take >> k) & 1u) qn[LCHK(b++, P.n, 105)] = v[k];
 }
 
 // Warp-collective: expand `count` entries of one local frontier (level 0 of a
@@ -139,13 +154,13 @@ __device__ __forceinline__ void expand_local(const LParams& P, int s, bool from_
     long long start = 0;
     if (have) {
       if (from_global) {
-        u = gq[lo + i];
+        u = gq[LCHK(lo + i, P.n, 106)];
         const unsigned bit = 1u << (u & 31);
-        atomicAnd(qb + (u >> 5), ~bit);  // leaves the queue: it may be queued again from now on
+        atomicAnd(qb + LCHK(u >> 5, P.nw, 107), ~bit);  // leaves the queue: it may be queued again from now on
         row_of<RP>(P, u, start, deg, n0, n1);
-        label = (int)ld_relaxed_u32(P.dist + u);
+        label = (int)ld_relaxed_u32(P.dist + LCHK(u, P.n, 108));
       } else {
-        const LocalEntry& e = A[i];
+        const LocalEntry& e = A[LCHK(i, P.cap_local, 109)];
         u = e.u;
         label = e.label;
         start = e.start;
@@ -153,7 +168,7 @@ __device__ __forceinline__ void expand_local(const LParams& P, int s, bool from_
         n0 = e.n0;
         n1 = e.n1;
         // A lower label means another thread lowered it and expands u itself.
-        if ((int)ld_relaxed_u32(P.dist + u) < label) have = false;
+        if ((int)ld_relaxed_u32(P.dist + LCHK(u, P.n, 110)) < label) have = false;
       }
     }
     if (!have) deg = 0;
@@ -180,7 +195,7 @@ __device__ __forceinline__ void expand_local(const LParams& P, int s, bool from_
           const int h0 = __shfl_sync(kFull, n0, o), h1 = __shfl_sync(kFull, n1, o);
           lab[k] = __shfl_sync(kFull, label, o) + 1;
           v[k] = -1;
-          if (e < total) v[k] = off < skip ? (off == 0 ? h0 : h1) : __ldg(P.col + so + off);
+          if (e < total) v[k] = off < skip ? (off == 0 ? h0 : h1) : __ldg(P.col + LCHK(so + off, P.m, 111));
         }
         unsigned imp = 0;
         long long rs[4];
@@ -191,7 +206,7 @@ __device__ __forceinline__ void expand_local(const LParams& P, int s, bool from_
           rd[k] = 0;
           r0[k] = r1[k] = -1;
           if (v[k] >= 0) {
-            const unsigned old = atomicMin(P.dist + v[k], (unsigned)lab[k]);
+            const unsigned old = atomicMin(P.dist + LCHK(v[k], P.n, 112), (unsigned)lab[k]);
             if (old > (unsigned)lab[k]) imp |= 1u << k;
             if (to_local) row_of<RP>(P, v[k], rs[k], rd[k], r0[k], r1[k]);  // issued with the claim
             if (STATS) acc.examined += 1;
@@ -213,7 +228,7 @@ __device__ __forceinline__ void expand_local(const LParams& P, int s, bool from_
           for (int k = 0; k < 4; ++k)
             if ((imp >> k) & 1u) {
               if (bb < P.cap_local) {
-                LocalEntry& d = B[bb];
+                LocalEntry& d = B[LCHK(bb, P.cap_local, 113)];
                 d.start = rs[k];
                 d.deg = rd[k];
                 d.label = lab[k];
@@ -395,6 +410,23 @@ int run_local(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_sta
   GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
   GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, stream));
   return BFS_OK;
+}
+
+bool bounds_read_local(unsigned long long* first, bool reset) {
+#ifdef GBFS_DEBUG_BOUNDS
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_local_bounds_err, sizeof(v)) != cudaSuccess) v = 0;
+  if (reset) {
+    const unsigned long long z = 0;
+    cudaMemcpyToSymbol(g_local_bounds_err, &z, sizeof(z));
+  }
+  *first = v;
+  return true;
+#else
+  *first = 0;
+  (void)reset;
+  return false;
+#endif
 }
 
 }  // namespace gbfs

@@ -104,6 +104,7 @@ int setup_device(int dev, void** scratch, int* num_sms) {
 
 extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const int32_t* col_idx, int64_t n,
                                   int64_t m, int32_t src, int32_t* dist, void* stream) {
+  GBFS_NVTX("bfs_single_noalloc");
   using namespace gbfs;
   if (!row_ptr || !dist || (m > 0 && !col_idx)) return BFS_EINVAL;
   if (row_ptr_bits != 32 && row_ptr_bits != 64) return BFS_EINVAL;
@@ -169,6 +170,8 @@ extern "C" int bfs_single_noalloc(const void* row_ptr, int row_ptr_bits, const i
   K.need_qv = K.policy != BFS_POLICY_TD_ONLY;
   K.timeout_ns = (long long)p.timeout_ms * 1000000ll;
   K.barrier_extra = 0;
+  K.col_cap = (m + 3) / 4 * 4;  // 16-byte loads stay inside the block holding the last entry
+  K.mg_cap = m / 8192 + 2;
   // The previous call left its control block behind: it must start at zero.
   GBFS_CUDA(cudaMemsetAsync(K.ctrl, 0, sizeof(Ctrl), s));
   const int mask_grid = num_sms * 4;

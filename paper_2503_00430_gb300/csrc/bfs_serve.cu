@@ -363,6 +363,7 @@ void graph_worker(bfs_server* S, GraphEntry* ge) {
 extern "C" {
 
 int bfs_serve_create(size_t mem_budget, const bfs_params* params, bfs_server** out) {
+  GBFS_NVTX("bfs_serve_create");
   if (!out) return BFS_EINVAL;
   *out = nullptr;
   bfs_server* S = new bfs_server();
@@ -383,6 +384,7 @@ int bfs_serve_create(size_t mem_budget, const bfs_params* params, bfs_server** o
 }
 
 int bfs_serve_add_graph(bfs_server* S, bfs_graph* g, int32_t* graph_id) {
+  GBFS_NVTX("bfs_serve_add_graph");
   if (!S || !g || !graph_id) return BFS_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) return BFS_EINVAL;
@@ -395,6 +397,7 @@ int bfs_serve_add_graph(bfs_server* S, bfs_graph* g, int32_t* graph_id) {
 }
 
 int bfs_serve_submit(bfs_server* S, int32_t graph_id, int32_t src, int32_t* dist_out, uint64_t* ticket) {
+  GBFS_NVTX("bfs_serve_submit");
   if (!S || !dist_out || !ticket) return BFS_EINVAL;
   const bool host_out = !gbfs::is_device_pointer(dist_out);
   std::lock_guard<std::mutex> lk(S->mu);
@@ -434,6 +437,7 @@ int bfs_serve_poll(bfs_server* S, uint64_t ticket, int* done, bfs_query_stats* s
 }
 
 int bfs_serve_wait(bfs_server* S, uint64_t ticket, int64_t timeout_us, bfs_query_stats* stats) {
+  GBFS_NVTX("bfs_serve_wait");
   if (!S) return BFS_EINVAL;
   std::unique_lock<std::mutex> lk(S->mu);
   auto it = S->tickets.find(ticket);
@@ -454,6 +458,7 @@ int bfs_serve_wait(bfs_server* S, uint64_t ticket, int64_t timeout_us, bfs_query
 }
 
 void bfs_serve_destroy(bfs_server* S) {
+  GBFS_NVTX("bfs_serve_destroy");
   if (!S) return;
   std::vector<GraphEntry*> ges;
   {

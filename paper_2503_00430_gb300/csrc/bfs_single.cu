@@ -34,12 +34,40 @@ namespace {
 
 using namespace dev;
 
+// Bounds-checked build (GBFS_DEBUG_BOUNDS, the stand-in for a memory checker):
+// every data-dependent global index of the kernels below is checked against
+// its array; the first out-of-range index is recorded in a device word
+// (bit 63, site << 48, low 48 bits of the index) and the access goes to element
+// 0 instead, so the kernel still completes.  Release builds compile the
+// checks away (the macros are the index itself).
+#ifdef GBFS_DEBUG_BOUNDS
+__device__ unsigned long long g_bounds_err;
+__device__ __forceinline__ long long bchk(long long i, long long lim, int site) {
+  if (i >= 0 && i < lim) return i;
+  atomicCAS(&g_bounds_err, 0ull,
+            (1ull << 63) | ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+  return 0;
+}
+#define GBFS_CHK(i, lim, site) bchk((long long)(i), (long long)(lim), (site))
+#else
+#define GBFS_CHK(i, lim, site) (i)
+#endif
+#define BV(i, site) GBFS_CHK(i, P.n, site)          // per-vertex arrays (head, dist, level bytes, id maps)
+#define BRP(i, site) GBFS_CHK(i, P.n + 1, site)     // row pointers
+#define BW(i, site) GBFS_CHK(i, P.nw, site)         // bitmap words (visited, next frontier, mask)
+#define BWF(i, site) GBFS_CHK(i, P.nw, site)        // frontier bitmap words
+#define BQ(i, site) GBFS_CHK(i, P.n, site)          // vertex queues
+#define BIT(i, site) GBFS_CHK(i, P.cap, site)       // work items
+#define BMG(i, site) GBFS_CHK(i, P.mg_cap, site)    // hub records
+#define BCOL(i, site) GBFS_CHK(i, P.col_cap, site)  // one neighbour id
+#define BCOL4(i, site) GBFS_CHK(i, P.col_cap - 3, site)  // four neighbour ids from index i
+
 
 // The level of vertex v is L + 1: a level byte while the search keeps them
 // (direct = false), else its int32 distance.
 __device__ __forceinline__ void mark_level(const KParams& P, bool direct, int v, int L) {
-  if (direct) P.dist[P.old_of ? P.old_of[v] : v] = L + 1;
-  else st_u8_last(P.lv8 + v, (unsigned)(L + 1));
+  if (direct) P.dist[BV(P.old_of ? P.old_of[BV(v, 1)] : v, 2)] = L + 1;
+  else st_u8_last(P.lv8 + BV(v, 3), (unsigned)(L + 1));
 }
 
 __device__ __forceinline__ unsigned long long pack_item(long long start, int len) {
@@ -136,9 +164,9 @@ __device__ __noinline__ void init_phase(const KParams& P) {
   }
   const int sw = P.src >> 5;
   for (long long w = tid; w < P.nw; w += nth) {
-    unsigned x = __ldg(P.init_vis + w);
+    unsigned x = __ldg(P.init_vis + BW(w, 4));
     if (w == sw) x |= 1u << (P.src & 31);
-    P.vis[w] = x;
+    P.vis[BW(w, 5)] = x;
   }
 }
 
@@ -153,7 +181,7 @@ __device__ __noinline__ void expand_phase(const KParams& P) {
   if (P.new_of) {
     auto level_of = [&](int nv) -> int {
       if ((long long)nv >= P.n_live && nv != P.src) return -1;
-      const int t = P.lv8[nv];
+      const int t = P.lv8[BV(nv, 6)];
       return t == 255 ? -1 : t;
     };
     if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
@@ -166,7 +194,7 @@ __device__ __noinline__ void expand_phase(const KParams& P) {
       }
       done = n4 << 2;
     }
-    for (long long i = done + tid; i < n; i += nth) P.dist[i] = level_of(P.new_of[i]);
+    for (long long i = done + tid; i < n; i += nth) P.dist[i] = level_of(P.new_of[BV(i, 7)]);
     return;
   }
   if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
@@ -194,8 +222,8 @@ __device__ __noinline__ void expand_phase(const KParams& P) {
 // Level-0 frontier {src}: vertex queue, work items and counters of slot 0.
 template <typename RP>
 __device__ __noinline__ void seed_phase(const KParams& P) {
-  const long long s = rp_at<RP>(P.rp, P.src);
-  const long long d = rp_at<RP>(P.rp, (long long)P.src + 1) - s;
+  const long long s = rp_at<RP>(P.rp, BRP(P.src, 8));
+  const long long d = rp_at<RP>(P.rp, BRP((long long)P.src + 1, 9)) - s;
   Slot* sl = &P.ctrl->slot[0];
   P.qv0[0] = P.src;
   unsigned long long nsm = 0, nlg = 0;
@@ -211,7 +239,7 @@ __device__ __noinline__ void seed_phase(const KParams& P) {
     for (long long c = 0; c * P.chunk < d; ++c) {
       long long len = d - c * P.chunk;
       if (len > P.chunk) len = P.chunk;
-      P.it0[P.cap - 1 - nlg] = pack_item(s + c * P.chunk, (int)len);
+      P.it0[BIT(P.cap - 1 - nlg, 10)] = pack_item(s + c * P.chunk, (int)len);
       ++nlg;
     }
   }
@@ -246,9 +274,10 @@ __device__ __forceinline__ void append_hubs(const KParams& P, unsigned mask, con
 #pragma unroll
   for (int k = 0; k < 4; ++k)
     if ((mask >> k) & 1u) {
-      mgn[r].start = s[k];
-      mgn[r].deg = d[k];
-      mgn[r].base = c;
+      const long long rr = BMG(r, 11);
+      mgn[rr].start = s[k];
+      mgn[rr].deg = d[k];
+      mgn[rr].base = c;
       ++r;
       c += (unsigned long long)((d[k] + P.chunk - 1) / P.chunk);
     }
@@ -267,12 +296,12 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, bool direct, 
                                           unsigned long long* itn, MegaRec* mgn) {
   unsigned cur[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) cur[k] = c[k] >= 0 ? ld_relaxed_u32(P.vis + (c[k] >> 5)) : kFull;
+  for (int k = 0; k < 4; ++k) cur[k] = c[k] >= 0 ? ld_relaxed_u32(P.vis + BW(c[k] >> 5, 12)) : kFull;
   unsigned old[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const unsigned bit = 1u << (c[k] & 31);
-    old[k] = (c[k] >= 0 && !(cur[k] & bit)) ? atomicOr(P.vis + (c[k] >> 5), bit) : kFull;
+    old[k] = (c[k] >= 0 && !(cur[k] & bit)) ? atomicOr(P.vis + BW(c[k] >> 5, 13), bit) : kFull;
   }
   unsigned cl = 0;
 #pragma unroll
@@ -288,12 +317,12 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, bool direct, 
     if ((cl >> k) & 1u) {
       mark_level(P, direct, c[k], L);
       if (P.head) {
-        const int4 h = __ldg(P.head + c[k]);
+        const int4 h = __ldg(P.head + BV(c[k], 14));
         s[k] = h.z;
         d[k] = h.w;
       } else {
-        s[k] = rp_at<RP>(P.rp, c[k]);
-        d[k] = (int)(rp_at<RP>(P.rp, (long long)c[k] + 1) - s[k]);
+        s[k] = rp_at<RP>(P.rp, BRP(c[k], 15));
+        d[k] = (int)(rp_at<RP>(P.rp, BRP((long long)c[k] + 1, 16)) - s[k]);
       }
     }
   }
@@ -329,13 +358,13 @@ __device__ __forceinline__ void td_visit4(const KParams& P, int L, bool direct, 
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (!((cl >> k) & 1u)) continue;
-    if (P.need_qv) qvn[qi++] = c[k];
+    if (P.need_qv) qvn[BQ(qi++, 17)] = c[k];
     if (d[k] > 0 && d[k] < P.small_max) {
-      itn[si++] = pack_item(s[k], d[k]);
+      itn[BIT(si++, 18)] = pack_item(s[k], d[k]);
     } else if (d[k] >= P.small_max && !((hubs >> k) & 1u)) {
       for (int o = 0; o < d[k]; o += P.chunk) {
         const int len = d[k] - o < P.chunk ? d[k] - o : P.chunk;
-        itn[P.cap - 1 - (long long)(li++)] = pack_item(s[k] + o, len);
+        itn[BIT(P.cap - 1 - (long long)(li++), 19)] = pack_item(s[k] + o, len);
       }
     }
   }
@@ -351,7 +380,7 @@ __device__ __forceinline__ void td_span(const KParams& P, int L, bool direct, lo
   for (long long base = s & ~3ll; base < e; base += 128) {
     const long long j = base + 4 * (long long)lane;
     int4 q = make_int4(-1, -1, -1, -1);
-    if (j < e) q = ldg4_first(P.col + j);
+    if (j < e) q = ldg4_first(P.col + BCOL4(j, 20));
     const int c[4] = {(j >= s && j < e) ? q.x : -1, (j + 1 >= s && j + 1 < e) ? q.y : -1,
                       (j + 2 >= s && j + 2 < e) ? q.z : -1, (j + 3 >= s && j + 3 < e) ? q.w : -1};
     td_visit4<RP>(P, L, direct, c, out, qvn, itn, mgn);
@@ -384,7 +413,7 @@ __device__ void td_phase(const KParams& P, int L, bool direct, unsigned long lon
       // 32 small items; their entries are dealt to the lanes through an
       // exclusive scan of the lengths, 128 per step (four per lane).
       const unsigned long long i = (unsigned long long)u * 32ull + lane;
-      const unsigned long long item = i < nsmall ? it[i] : 0ull;
+      const unsigned long long item = i < nsmall ? it[BIT(i, 21)] : 0ull;
       const long long s = (long long)(item >> 16);
       const int len = (int)(item & 0xffffull);
       const int incl = warp_incl_scan(len);
@@ -399,12 +428,12 @@ __device__ void td_phase(const KParams& P, int L, bool direct, unsigned long lon
           const int o = owner_of(excl, e);
           const long long so = __shfl_sync(kFull, s, o);
           const int exo = __shfl_sync(kFull, excl, o);
-          c[k] = e < total ? __ldg(P.col + so + (e - exo)) : -1;
+          c[k] = e < total ? __ldg(P.col + BCOL(so + (e - exo), 22)) : -1;
         }
         td_visit4<RP>(P, L, direct, c, out, qvn, itn, mgn);
       }
     } else if (u < ngroups + (long long)nlarge) {
-      const unsigned long long item = it[P.cap - 1 - (u - ngroups)];
+      const unsigned long long item = it[BIT(P.cap - 1 - (u - ngroups), 23)];
       const long long s = (long long)(item >> 16);
       const int len = (int)(item & 0xffffull);
       if (STATS && lane == 0) acc.edges += (unsigned long long)len;
@@ -417,15 +446,16 @@ __device__ void td_phase(const KParams& P, int L, bool direct, unsigned long lon
       while (hi - lo > 1) {
         const long long step = (hi - lo + 31) / 32;
         const long long idx = lo + (long long)lane * step;
-        const bool ok = idx < hi && (long long)mg[idx].base <= t;
+        const bool ok = idx < hi && (long long)mg[BMG(idx, 24)].base <= t;
         const unsigned bm = __ballot_sync(kFull, ok);
         const long long k = 31 - __clz(bm);
         lo = lo + k * step;
         hi = lo + step < hi ? lo + step : hi;
       }
-      const long long o = (t - (long long)mg[lo].base) * P.chunk;
-      const long long hd = mg[lo].deg;
-      const long long s = mg[lo].start + o;
+      const long long lr = BMG(lo, 25);
+      const long long o = (t - (long long)mg[lr].base) * P.chunk;
+      const long long hd = mg[lr].deg;
+      const long long s = mg[lr].start + o;
       const long long e = s + (hd - o < P.chunk ? hd - o : P.chunk);
       if (STATS && lane == 0) acc.edges += (unsigned long long)(e - s);
       td_span<RP>(P, L, direct, s, e, out, qvn, itn, mgn);
@@ -436,9 +466,7 @@ __device__ void td_phase(const KParams& P, int L, bool direct, unsigned long lon
 
 // ---------------------------------------------------------------- bottom-up
 
-__device__ __forceinline__ bool in_frontier(const unsigned* front, int u) {
-  return (front[u >> 5] >> (u & 31)) & 1u;
-}
+#define in_frontier(front, u) ((((front)[BWF((u) >> 5, 26)]) >> ((u) & 31)) & 1u)
 
 // Shared-memory staging of one warp in a bottom-up batch.
 #ifndef GBFS_BU_U
@@ -500,12 +528,12 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
     for (int done = 0; pl > 0 && done < P.bu_thread_max;) {
       const long long a = ps & ~3ll;
       const int off = (int)(ps - a);
-      const int4 q0 = ldg4_first(P.col + a);
-      const int4 q1 = pl > 4 - off ? ldg4_first(P.col + a + 4) : make_int4(0, 0, 0, 0);
+      const int4 q0 = ldg4_first(P.col + BCOL4(a, 27));
+      const int4 q1 = pl > 4 - off ? ldg4_first(P.col + BCOL4(a + 4, 28)) : make_int4(0, 0, 0, 0);
       const int c8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
       bool h[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) h[t] = t >= off && t - off < pl && ((front[c8[t] >> 5] >> (c8[t] & 31)) & 1u);
+      for (int t = 0; t < 8; ++t) h[t] = t >= off && t - off < pl && in_frontier(front, c8[t]);
       int ft = -1;
 #pragma unroll
       for (int t = 7; t >= 0; --t)
@@ -540,12 +568,12 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
         const long long so = __shfl_sync(kFull, ps, o[k]);
         const int exo = __shfl_sync(kFull, excl, o[k]);
         want[k] = ei < total && ((pend >> o[k]) & 1u);
-        u[k] = want[k] ? __ldg(P.col + so + (ei - exo)) : 0;
+        u[k] = want[k] ? __ldg(P.col + BCOL(so + (ei - exo), 29)) : 0;
       }
       bool hk[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const unsigned fw = want[k] ? front[u[k] >> 5] : 0u;
+        const unsigned fw = want[k] ? front[BWF(u[k] >> 5, 30)] : 0u;
         hk[k] = (fw >> (u[k] & 31)) & 1u;
       }
       unsigned mine = 0;
@@ -586,8 +614,8 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
       for (long long a = hs & ~3ll; a < he; a += 256) {
         const long long j0 = a + 8 * (long long)lane;
         int4 q0 = make_int4(0, 0, 0, 0), q1 = make_int4(0, 0, 0, 0);
-        if (j0 < he) q0 = ldg4_first(P.col + j0);
-        if (j0 + 4 < he) q1 = ldg4_first(P.col + j0 + 4);
+        if (j0 < he) q0 = ldg4_first(P.col + BCOL4(j0, 31));
+        if (j0 + 4 < he) q1 = ldg4_first(P.col + BCOL4(j0 + 4, 32));
         const int c8[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
         bool h8[8];
 #pragma unroll
@@ -643,20 +671,20 @@ __device__ __forceinline__ void bu_issue_round(const KParams& P, BuWarpSmem& sm,
 #pragma unroll
   for (int k = 0; k < kBuU; ++k) {
     sm.vbuf[b][32 * k + lane] = v[k];
-    cp_async16_first(&sm.hbuf[b][32 * k + lane], v[k] >= 0 ? P.head + v[k] : P.head, v[k] >= 0 ? 16 : 0);
+    cp_async16_first(&sm.hbuf[b][32 * k + lane], v[k] >= 0 ? P.head + BV(v[k], 33) : P.head, v[k] >= 0 ? 16 : 0);
   }
 }
 
 // Frontier words holding the two head neighbours of this lane's vertices in
 // round buffer b (0 where a neighbour is missing or the slot is empty).
-__device__ __forceinline__ void bu_probe_words(const BuWarpSmem& sm, const unsigned* front, int b,
+__device__ __forceinline__ void bu_probe_words(const KParams& P, const BuWarpSmem& sm, const unsigned* front, int b,
                                                unsigned (&w0)[kBuU], unsigned (&w1)[kBuU]) {
   const unsigned lane = lane_id();
 #pragma unroll
   for (int k = 0; k < kBuU; ++k) {
     const int4 h = sm.vbuf[b][32 * k + lane] >= 0 ? sm.hbuf[b][32 * k + lane] : make_int4(-1, -1, 0, 0);
-    w0[k] = h.x >= 0 ? front[h.x >> 5] : 0u;
-    w1[k] = h.y >= 0 ? front[h.y >> 5] : 0u;
+    w0[k] = h.x >= 0 ? front[BWF(h.x >> 5, 34)] : 0u;
+    w1[k] = h.y >= 0 ? front[BWF(h.y >> 5, 35)] : 0u;
   }
 }
 
@@ -694,7 +722,7 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
     }
     if (nrounds > 0) {
       cp_async_wait<kDepth - 1>();
-      bu_probe_words(sm, front, 0, pw0, pw1);
+      bu_probe_words(P, sm, front, 0, pw0, pw1);
     }
   }
   for (int r = 0; r < nrounds; ++r) {
@@ -712,7 +740,7 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
       unsigned nw0[kBuU] = {}, nw1[kBuU] = {};
       if (r + 1 < nrounds) {
         cp_async_wait<kDepth - 1>();
-        bu_probe_words(sm, front, (r + 1) % kNBuf, nw0, nw1);
+        bu_probe_words(P, sm, front, (r + 1) % kNBuf, nw0, nw1);
       }
       const int buf = r % kNBuf;
 #pragma unroll
@@ -754,15 +782,15 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
         s[k] = 0;
         e[k] = 0;
         if (v[k] >= 0) {
-          s[k] = rp_at<RP>(P.rp, v[k]);
-          e[k] = rp_at<RP>(P.rp, (long long)v[k] + 1);
+          s[k] = rp_at<RP>(P.rp, BRP(v[k], 36));
+          e[k] = rp_at<RP>(P.rp, BRP((long long)v[k] + 1, 37));
         }
       }
       int4 q[kBuU];
 #pragma unroll
       for (int k = 0; k < kBuU; ++k) {
         q[k] = make_int4(0, 0, 0, 0);
-        if (e[k] > s[k]) q[k] = __ldg(reinterpret_cast<const int4*>(P.col + (s[k] & ~3ll)));
+        if (e[k] > s[k]) q[k] = __ldg(reinterpret_cast<const int4*>(P.col + BCOL4(s[k] & ~3ll, 38)));
       }
       unsigned f[kBuU][4];
 #pragma unroll
@@ -772,7 +800,7 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const bool ok = a0 + t >= s[k] && a0 + t < e[k];
-          f[k][t] = ok ? ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u) : 0u;
+          f[k][t] = ok ? in_frontier(front, c4[t]) : 0u;
         }
       }
 #pragma unroll
@@ -807,8 +835,8 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
   __syncwarp();
   const unsigned nx = sm.next[lane];
   if (w < P.nw) {
-    next[w] = nx;
-    if (nx) P.vis[w] = vw | nx;  // this warp is the only writer of its batch's words
+    next[BW(w, 39)] = nx;
+    if (nx) P.vis[BW(w, 40)] = vw | nx;  // this warp is the only writer of its batch's words
   }
   __syncwarp();
 }
@@ -816,7 +844,7 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
 // Visited word of lane `lane` in the batch starting at word w0 (all-set past the end).
 __device__ __forceinline__ unsigned batch_word(const KParams& P, long long w0) {
   const long long w = w0 + lane_id();
-  return w < P.nw ? P.vis[w] : kFull;
+  return w < P.nw ? P.vis[BW(w, 48)] : kFull;
 }
 
 // Bottom-up level.  Batches of 32 words go to warps statically (interleaved:
@@ -886,12 +914,12 @@ __device__ void zero_words(unsigned* p, long long nw) {
 }
 
 // Queue -> bitmap: set the bit of every vertex of F (nv entries of qv).
-__device__ void scatter_phase(const int* qv, long long nv, unsigned* bm) {
+__device__ void scatter_phase(const KParams& P, const int* qv, long long nv, unsigned* bm) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   for (long long i = tid; i < nv; i += nth) {
-    const int v = qv[i];
-    atomicOr(bm + (v >> 5), 1u << (v & 31));
+    const int v = qv[BQ(i, 41)];
+    atomicOr(bm + BW(v >> 5, 42), 1u << (v & 31));
   }
 }
 
@@ -947,12 +975,12 @@ __device__ __noinline__ void convert_phase(const KParams& P, int L, const unsign
       if (vw >= 0) {
         const int v = (int)(vw * 32 + (long long)nth_set_bit(aw, r));
         if (P.head) {
-          const int4 h = __ldg(P.head + v);
+          const int4 h = __ldg(P.head + BV(v, 43));
           s = h.z;
           d = h.w;
         } else {
-          s = rp_at<RP>(P.rp, v);
-          d = (int)(rp_at<RP>(P.rp, (long long)v + 1) - s);
+          s = rp_at<RP>(P.rp, BRP(v, 44));
+          d = (int)(rp_at<RP>(P.rp, BRP((long long)v + 1, 45)) - s);
         }
       }
       const int ni = (d + P.chunk - 1) / P.chunk;
@@ -971,12 +999,12 @@ __device__ __noinline__ void convert_phase(const KParams& P, int L, const unsign
       if (lane == 0)
         b_items = atomicAdd(&out->items, (unsigned long long)__popc(smask) | ((unsigned long long)lg_tot << 32));
       b_items = __shfl_sync(kFull, b_items, 0);
-      if (nsm) itn[(b_items & 0xffffffffull) + __popc(smask & lt)] = pack_item(s, d);
+      if (nsm) itn[BIT((b_items & 0xffffffffull) + __popc(smask & lt), 46)] = pack_item(s, d);
       if (nlg) {
         unsigned long long bb = (b_items >> 32) + (unsigned long long)(lg_incl - nlg);
         for (int o = 0; o < d; o += P.chunk) {
           const int len = d - o < P.chunk ? d - o : P.chunk;
-          itn[P.cap - 1 - (long long)(bb++)] = pack_item(s + o, len);
+          itn[BIT(P.cap - 1 - (long long)(bb++), 47)] = pack_item(s + o, len);
         }
       }
     }
@@ -1129,7 +1157,7 @@ __global__ void __launch_bounds__(1024) bfs_persistent_kernel(KParams P) {
       // top-down -> bottom-up: the new frontier's vertex queue becomes bitmap bm0
       zero_words(P.bm0, P.nw);
       if (!grid_barrier(P, epoch)) return;
-      scatter_phase(((L + 1) & 1) ? P.qv1 : P.qv0, nf, P.bm0);
+      scatter_phase(P, ((L + 1) & 1) ? P.qv1 : P.qv0, nf, P.bm0);
       if (!grid_barrier(P, epoch)) return;
     } else if (action == 2) {
       // bottom-up -> top-down: work items from the new frontier's bitmap
@@ -1184,8 +1212,8 @@ __global__ void __launch_bounds__(1024) k_zero_words(unsigned* p, long long nw) 
 
 __global__ void __launch_bounds__(1024) k_expand(KParams P) { expand_phase(P); }
 
-__global__ void __launch_bounds__(1024) k_scatter(const int* qv, long long nv, unsigned* bm) {
-  scatter_phase(qv, nv, bm);
+__global__ void __launch_bounds__(1024) k_scatter(KParams P, const int* qv, long long nv, unsigned* bm) {
+  scatter_phase(P, qv, nv, bm);
 }
 
 template <typename RP>
@@ -1264,6 +1292,8 @@ static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, 
   K.need_qv = K.policy != BFS_POLICY_TD_ONLY;
   K.timeout_ns = (long long)p.timeout_ms * 1000000ll;
   K.barrier_extra = p.test_barrier_extra;
+  K.col_cap = g->m + 4;  // both the uploaded lists and the renumbered copy carry >= 4 spare entries
+  K.mg_cap = g->m / 8192 + 2;
 }
 
 template <typename RP, bool STATS>
@@ -1335,7 +1365,7 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
     converted = 0;
     if (td && !ntd) {
       k_zero_words<<<grid, block, 0, stream>>>(K.bm0, K.nw);
-      k_scatter<<<grid, block, 0, stream>>>(((L + 1) & 1) ? K.qv1 : K.qv0, nf, K.bm0);
+      k_scatter<<<grid, block, 0, stream>>>(K, ((L + 1) & 1) ? K.qv1 : K.qv0, nf, K.bm0);
       GBFS_CUDA(cudaGetLastError());
       fb = 0;
       converted = 1;
@@ -1518,6 +1548,23 @@ int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_st
     GBFS_CUDA(cudaMemcpy(levels, ws.lst, sizeof(bfs_level_stat) * (size_t)nl, cudaMemcpyDeviceToHost));
   }
   return BFS_OK;
+}
+
+bool bounds_read_single(unsigned long long* first, bool reset) {
+#ifdef GBFS_DEBUG_BOUNDS
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_err, sizeof(v)) != cudaSuccess) v = 0;
+  if (reset) {
+    const unsigned long long z = 0;
+    cudaMemcpyToSymbol(g_bounds_err, &z, sizeof(z));
+  }
+  *first = v;
+  return true;
+#else
+  *first = 0;
+  (void)reset;
+  return false;
+#endif
 }
 
 }  // namespace gbfs

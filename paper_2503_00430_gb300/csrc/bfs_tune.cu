@@ -127,6 +127,7 @@ using namespace gbfs;
 
 extern "C" int bfs_tune(bfs_graph* g, const int32_t* srcs, int32_t k, const bfs_params* base, bfs_params* out,
                         bfs_tune_report* report) {
+  GBFS_NVTX("bfs_tune");
   if (!g || !srcs || k <= 0 || !out) return BFS_EINVAL;
   for (int i = 0; i < k; ++i)
     if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return BFS_EINVAL;
@@ -211,6 +212,7 @@ extern "C" int bfs_tune(bfs_graph* g, const int32_t* srcs, int32_t k, const bfs_
 
 extern "C" int bfs_tune_multi(bfs_graph* g, const int32_t* srcs, int32_t k, int dist_bits, const bfs_params* base,
                               bfs_params* out, bfs_tune_report* report) {
+  GBFS_NVTX("bfs_tune_multi");
   if (!g || !srcs || k <= 0 || !out || (dist_bits != 8 && dist_bits != 32)) return BFS_EINVAL;
   for (int i = 0; i < k; ++i)
     if (srcs[i] < 0 || (int64_t)srcs[i] >= g->n) return BFS_EINVAL;
@@ -265,6 +267,7 @@ extern "C" int bfs_tune_multi(bfs_graph* g, const int32_t* srcs, int32_t k, int 
 
 extern "C" int bfs_tune_graphset(bfs_graphset* set, const int32_t* srcs, const bfs_params* base, bfs_params* out,
                                  bfs_tune_report* report) {
+  GBFS_NVTX("bfs_tune_graphset");
   if (!set || !srcs || !out) return BFS_EINVAL;
   bfs_params cur;
   if (base) cur = *base; else bfs_params_default(&cur);

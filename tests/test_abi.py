@@ -65,3 +65,29 @@ def test_graph_class_keys():
     assert B.graph_class(4096 * 4096, 67092480).startswith("large_diameter")
     assert B.graph_class(1 << 25, 1047207640) == "dense_n2e25"
     assert B.graph_class(1 << 24, 268435294) == "sparse_n2e24"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C sizes and field offsets (a tiny C
+    program compiled against include/bfs.h prints them)."""
+    import paper_2503_00430_gb300 as B
+    structs = {"bfs_params": B.bfs_params, "bfs_stats": B.bfs_stats, "bfs_level_stat": B.bfs_level_stat,
+               "bfs_multi_stats": B.bfs_multi_stats, "bfs_dup_level": B.bfs_dup_level,
+               "bfs_dup_stats": B.bfs_dup_stats, "bfs_graphset_stats": B.bfs_graphset_stats,
+               "bfs_query_stats": B.bfs_query_stats, "bfs_tune_report": B.bfs_tune_report}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bfs.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)

@@ -262,3 +262,42 @@ def test_renumbered_copy_deep_search(bfs):
         n = len(rp) - 1
         check(bfs, rp, col, [0, n // 3, n - 1], policies={k: POLICIES[k] for k in ("auto", "edges")},
               launches=(0, 1), extra=dict(relabel=1), check_stats=False)
+
+
+def _big_star():
+    """Centre 0 with 2^20 + 300 leaves: one list longer than 2^20 entries (a hub record of
+    more than 4096 chunk tickets in top-down levels, a whole-warp scan in bottom-up ones)."""
+    n = (1 << 20) + 301
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1] = n - 1
+    rp[2:] = n - 1 + np.arange(1, n, dtype=np.int64)
+    col = np.concatenate([np.arange(1, n, dtype=np.int32), np.zeros(n - 1, dtype=np.int32)])
+    return rp, col
+
+
+def test_hub_longer_than_2_pow_20(bfs):
+    rp, col = _big_star()
+    pol = {k: POLICIES[k] for k in ("td_only", "edges", "bu_from_1", "frontier")}
+    check(bfs, rp, col, [0, 7, len(rp) - 2], policies=pol)
+    check(bfs, rp, col, [0, 7], policies=pol, launches=(0,), extra=dict(relabel=1), check_stats=False)
+
+
+def _fan(n, k):
+    """Source 0 joined to vertices 1..k; every other vertex hangs off one of them (round robin)."""
+    edges = [(0, i) for i in range(1, k + 1)] + [(1 + (v - k - 1) % k, v) for v in range(k + 1, n)]
+    return G.csr_from_edges(n, edges)
+
+
+@pytest.mark.parametrize("k,bottom_up", [(20, True), (19, False)])
+def test_frontier_rule_at_exactly_n_over_20(bfs, k, bottom_up):
+    """n = 400 (divisible by 20) and |F_1| = k: the paper's rule (top-down while |F| is below 5 % of
+    n, read as the integer test 20 |F| < n) sends level 1 bottom-up at |F_1| = n/20 = 20 exactly and
+    keeps it top-down at 19; distances are the oracle's either way."""
+    rp, col = _fan(400, k)
+    check(bfs, rp, col, [0], policies={"frontier": dict(policy=1)})
+    g = bfs.bfs_graph_upload(rp, col)
+    d = torch.empty(400, dtype=torch.int32, device="cuda")
+    for launch in (0, 1):
+        _, lv = bfs.bfs_single_ex(g, 0, d, params=bfs.make_params(policy=1, launch=launch), level_cap=8)
+        assert lv[1]["frontier"] == k and lv[1]["direction"] == (1 if bottom_up else 0), (launch, lv[1])
+    g.free()
