@@ -190,6 +190,26 @@ def algorithmic_bytes(n, rp_bytes, levels, l2_bytes=L2_BYTES):
     return b
 
 
+def msbfs_bytes(n, n_live, lanes, rp_bytes, st, out_bytes_per_entry):
+    """Compulsory DRAM bytes of one multi-source call over `lanes` sources (W = ceil(lanes/64) mask
+    words per vertex, mb = 8W bytes per mask) from its counters `st` (bfs_multi_stats):
+
+    pull level: every scanned vertex's reached mask read and next-frontier mask written (2 mb per
+    vertex of degree > 0), a row pointer per vertex still missing a lane (RP * pull_active), and per
+    entry examined its id and the neighbour's frontier mask (4 + mb);
+    push level: per frontier vertex its mask and row-pointer pair (mb + 2 RP), per pushed entry its
+    id and the neighbour's accumulator (4 + mb);
+    every level: per vertex that gained a lane its reached-mask update and next-frontier mask (2 mb);
+    output: lanes * n entries written once.
+    Random mask gathers are counted in full (the masks, 32 bytes per vertex for 256 sources, do not
+    fit in L2 at these sizes)."""
+    mb = 8 * ((lanes + 63) // 64)
+    b = st["pull_levels"] * 2 * mb * n_live + rp_bytes * st["pull_active"] + (4 + mb) * st["pulled_edges"]
+    b += (mb + 2 * rp_bytes) * st["push_frontier"] + (4 + mb) * st["pushed_edges"]
+    b += 2 * mb * st["found"]
+    return b + lanes * n * out_bytes_per_entry
+
+
 def layout_bytes(n, rp_bytes, levels, head=True, queue=True):
     """DRAM bytes of one BFS for this library's own layout (reported beside
     the compulsory bytes, not used for the roofline): per-vertex level bytes
@@ -443,7 +463,14 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(rp, col, srcs, args.cpu_sample)
-    st0 = per_src[0]["stats"]
+    st_example = per_src[0]["stats"]
+    g.free()
+    del rp, col
+    msbfs = None
+    if args.workload == "rmat25" and not args.no_msbfs:
+        # The batched form on its own workload (one GPU per rank, replicas): uint8 rows, 3 calls.
+        msbfs = msbfs_measure(args, bits_list=(8,), reps=3)
+    st0 = st_example
     out = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -484,11 +511,12 @@ def run_ours(args):
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu
+    if msbfs is not None:
+        out["msbfs"] = msbfs
     if args.workload != "rmat25":
         out["metric"] = f"GTEPS (harmonic mean, 64 sources) {wname}"
     if rank == 0:
         print(json.dumps(out), flush=True)
-    g.free()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -587,47 +615,67 @@ def run_large(args):
     return 0
 
 
-def run_msbfs(args):
-    """Batched multi-source BFS: R-MAT scale 24, 256 sources per call, uint8 and int32 rows."""
+def msbfs_measure(args, bits_list=(8, 32), reps=None):
+    """Multi-source R-MAT s24 x 256 per call against 256 sequential single-source queries on the same
+    graph (both with their tuning-table parameters); per output width the time per call, BFS/s, the
+    ratio, the counters and the roofline on msbfs_bytes."""
     import torch
 
-    import graphgen
     import paper_2503_00430_gb300 as bfs
-    torch.cuda.set_device(0)
     rp, col, srcs = msbfs_workload()
-    n = len(rp) - 1
+    n, m = len(rp) - 1, len(col)
     g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | bfs.BFS_DEGREE_ORDER)
+    n_live = n - g.info()["isolated"]
+    del rp, col
+    sp = bfs.bfs_params_default() if args.no_tuned else bfs.tuned_params(None, g, "single")
     d = torch.empty(n, dtype=torch.int32, device="cuda")
     for s_ in srcs[:4]:
-        bfs.bfs_single(g, int(s_), d)
+        bfs.bfs_single_ex(g, int(s_), d, params=sp)
     torch.cuda.synchronize()
     e0, e1 = _events()
     e0.record()
     for s_ in srcs:
-        bfs.bfs_single(g, int(s_), d)
+        bfs.bfs_single_ex(g, int(s_), d, params=sp)
     e1.record()
     torch.cuda.synchronize()
     single_s = e0.elapsed_time(e1) / 1e3 / len(srcs)
-    out = {"single_source_bfs_per_s": 1.0 / single_s}
+    del d
+    hbm, peak_kind = peaks()
+    out = {"workload": "msbfs_rmat_s24_256src", "n": n, "m": m, "sources_per_call": 256,
+           "single_source_bfs_per_s": 1.0 / single_s}
     mp = bfs.bfs_params_default() if args.no_tuned else bfs.tuned_params(None, g, "multi")
-    for bits in (8, 32):
+    for bits in bits_list:
         buf = torch.empty((256, n), dtype=torch.uint8 if bits == 8 else torch.int32, device="cuda")
         st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits, params=mp)
         torch.cuda.synchronize()
         e0, e1 = _events()
         e0.record()
-        reps = max(1, args.steps // 4)
-        for _ in range(reps):
+        nrep = reps or max(1, args.steps // 4)
+        for _ in range(nrep):
             st = bfs.bfs_multi_ex(g, srcs, buf, dist_bits=bits, params=mp)
         e1.record()
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3 / reps
-        out[f"uint{bits}" if bits == 8 else "int32"] = {"ms_per_call": t * 1e3, "bfs_per_s": 256 / t,
-                                                        "vs_single_source": 256 / t * single_s, "stats": st}
+        t = e0.elapsed_time(e1) / 1e3 / nrep
+        byts = msbfs_bytes(n, n_live, 256, 8, st, bits // 8)
+        out["uint8" if bits == 8 else "int32"] = {
+            "ms_per_call": t * 1e3, "bfs_per_s": 256 / t, "vs_single_source": 256 / t * single_s, "stats": st,
+            "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": byts / t / 1e9 / hbm, "peak_kind": peak_kind, "bytes_per_call": byts,
+                         "kernels": "k_ms_pull, k_ms_heavy_chunks, k_ms_push, k_ms_apply, k_ms_write (one call)"}}
         del buf
+    g.free()
+    return out
+
+
+def run_msbfs(args):
+    """Batched multi-source BFS: R-MAT scale 24, 256 sources per call, uint8 and int32 rows."""
+    import torch
+
+    torch.cuda.set_device(0)
+    out = msbfs_measure(args)
     _json({"metric": "BFS/s, multi-source R-MAT s24 x 256 sources per call", "value": out["uint8"]["bfs_per_s"],
            "unit": "BFS/s", "higher_is_better": True, "n_gpus": 1, "dtype": "u8", "data": "synthetic",
-           "config": {"workload": "msbfs_rmat_s24_256src", "n": n, "m": int(len(col)), **out}})
+           "config": {k: v for k, v in out.items()}})
     return 0
 
 
@@ -839,6 +887,35 @@ def run_dup(args):
         out[name] = {"n": n, "m": int(len(col)), "overflows": len(res) - len(ok), "mean": agg, "sources": res}
         g.free()
         del rp, col
+    # The paper's variant proper: duplicates expanded again at the next level (BFS_DUP_EXPAND), on
+    # graphs small enough for its queues; per level the copies expanded against the distinct vertices.
+    faithful = {}
+    for name, make in (("rmat_s10", lambda: graphgen.rmat(10, EDGEFACTOR, 0.57, 0.19, 0.19, 1, 1)),
+                       ("rmat_s12", lambda: graphgen.rmat(12, EDGEFACTOR, 0.57, 0.19, 0.19, 1, 1)),
+                       ("rmat_s14", lambda: graphgen.rmat(14, EDGEFACTOR, 0.57, 0.19, 0.19, 1, 1)),
+                       ("er_2e14_d16", lambda: graphgen.erdos_renyi(1 << 14, 16.0, 5)),
+                       ("grid_64x64", lambda: graphgen.grid2d(64, 64))):
+        rp, col = make()
+        n = len(rp) - 1
+        g = bfs.bfs_graph_upload(rp, col)
+        d = torch.empty(n, dtype=torch.int32, device="cuda")
+        res = []
+        for src in graphgen.sources(rp, 4, 1007):
+            try:
+                st, lv = bfs.bfs_single_nonatomic(g, int(src), d, level_cap=1 << 14, expand_duplicates=True)
+            except bfs.BfsError as err:
+                if err.code != bfs.BFS_ENOMEM:
+                    raise
+                res.append({"src": int(src), "overflow": True, "queue_entries": n + int(len(col)) + 1})
+                continue
+            res.append({"src": int(src), "levels": st["levels"],
+                        "dup_fraction": (st["frontier_entries"] - st["unique"]) / st["unique"],
+                        "copies_per_vertex_by_level": [round(x["frontier"] / x["unique"], 3) for x in lv if x["unique"]],
+                        "edges_read_over_reached_degrees": st["edges"] / max(1, int(np.diff(rp)[d.cpu().numpy() >= 0].sum()))})
+        faithful[name] = {"n": n, "m": int(len(col)), "overflows": sum(1 for r in res if r.get("overflow")),
+                          "sources": res}
+        g.free()
+    out["expand_duplicates"] = faithful
     _json({"metric": "duplicate frontier entries of the non-atomic top-down BFS (fraction of distinct)",
            "value": out["rmat_s24"]["mean"]["dup_fraction"], "unit": "fraction", "higher_is_better": False,
            "n_gpus": 1, "dtype": "int32", "data": "synthetic", "config": {"workload": "nonatomic_duplicates", **out}})
@@ -866,6 +943,12 @@ def run_tune(args):
         done[wname] = bfs.tune_table_store(path, "single", p, rep, g.n, g.m, wname)
         g.free()
         del rp, col
+    rp, col, srcs = msbfs_workload()  # its single-source class: the sequential baseline of the batched form
+    g = bfs.bfs_graph_upload(rp, col, flags=bfs.BFS_VALIDATE | bfs.BFS_DEGREE_ORDER)
+    p, rep = bfs.bfs_tune(g, srcs[:64])
+    done["rmat_s24_single"] = bfs.tune_table_store(path, "single", p, rep, g.n, g.m, "rmat_s24_ef16_64src")
+    g.free()
+    del rp, col
     name, make = large_specs()[0]
     rp, col = make()
     g = bfs.bfs_graph_upload(rp.astype(np.int32), col, flags=bfs.BFS_VALIDATE)

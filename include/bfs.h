@@ -209,7 +209,11 @@ typedef struct bfs_multi_stats {
     int64_t pushed_edges;    /* entries read by push levels */
     int64_t pulled_edges;    /* entries read by pull levels */
     int64_t output_bytes;    /* bytes written to dist (every output row counted per window) */
-    int64_t reserved[4];
+    int64_t pull_active;     /* sum over pull levels of vertices still missing an active lane (the
+                                vertices whose lists a pull level reads) */
+    int64_t push_frontier;   /* sum over push levels of frontier vertices (whose lists are pushed) */
+    int64_t found;           /* sum over levels of vertices that gained at least one lane */
+    int64_t reserved[1];
 } bfs_multi_stats;
 
 /* Per-level counts of bfs_single_nonatomic (level L expands the frontier F_L). */
@@ -362,6 +366,22 @@ int bfs_parents(bfs_graph *g, const int32_t *dist, int32_t *parent, void *stream
  */
 int bfs_single_nonatomic(bfs_graph *g, int32_t src, int32_t *dist, bfs_dup_stats *stats, bfs_dup_level *levels,
                          int32_t level_cap, void *stream);
+
+/* bfs_single_nonatomic's treatment of duplicate frontier entries. */
+#define BFS_DUP_DEDUP 0   /* reduce each level's appended entries to distinct vertices (without atomics)
+                             before expanding them (bfs_single_nonatomic) */
+#define BFS_DUP_EXPAND 1  /* expand every appended entry, duplicates included, as the paper's variant does
+                             (Section 2: duplicates are processed again at the next level); a level's
+                             entries then also count the copies, and when they outgrow the queues
+                             (n + m + 1 entries) or the long-list records the call returns BFS_ENOMEM
+                             without writing past them */
+
+/* bfs_single_nonatomic with the duplicate mode (BFS_DUP_DEDUP or BFS_DUP_EXPAND).  Per level,
+ * levels[L].frontier counts the entries expanded at level L in BFS_DUP_EXPAND mode (the appended
+ * entries), levels[L].unique the distinct vertices among them, levels[L].edges the list entries read
+ * (every copy of a vertex reads its list again). */
+int bfs_single_nonatomic_ex(bfs_graph *g, int32_t src, int32_t *dist, int mode, bfs_dup_stats *stats,
+                            bfs_dup_level *levels, int32_t level_cap, void *stream);
 
 /* ---- autotuner ---- */
 

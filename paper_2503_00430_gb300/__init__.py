@@ -89,7 +89,8 @@ class bfs_multi_stats(ctypes.Structure):
     _fields_ = [
         ("levels", ctypes.c_int32), ("push_levels", ctypes.c_int32), ("pull_levels", ctypes.c_int32),
         ("groups", ctypes.c_int32), ("pushed_edges", ctypes.c_int64), ("pulled_edges", ctypes.c_int64),
-        ("output_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 4),
+        ("output_bytes", ctypes.c_int64), ("pull_active", ctypes.c_int64), ("push_frontier", ctypes.c_int64),
+        ("found", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1),
     ]
 
     def as_dict(self) -> dict:
@@ -176,6 +177,8 @@ _SIGNATURES = [
     ("bfs_parents", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("bfs_single_nonatomic", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_dup_stats),
                                             ctypes.POINTER(bfs_dup_level), _i32, _vp]),
+    ("bfs_single_nonatomic_ex", ctypes.c_int, [_vp, _i32, _vp, ctypes.c_int, ctypes.POINTER(bfs_dup_stats),
+                                               ctypes.POINTER(bfs_dup_level), _i32, _vp]),
     ("bfs_multi", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, _vp]),
     ("bfs_multi_ex", ctypes.c_int, [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.POINTER(bfs_params),
                                     ctypes.POINTER(bfs_multi_stats), _vp]),
@@ -401,12 +404,20 @@ def bfs_parents(g: Graph, dist, parent, stream=None) -> None:
     _check(load().bfs_parents(g.handle, _ptr(dist), _ptr(parent), _stream_handle(stream)), "bfs_parents")
 
 
-def bfs_single_nonatomic(g: Graph, src: int, dist, level_cap: int = 0, stats: bool = True, stream=None):
-    """The paper's non-atomic top-down BFS (duplicates allowed); returns (totals or None, per-level list)."""
+BFS_DUP_DEDUP = 0
+BFS_DUP_EXPAND = 1
+
+
+def bfs_single_nonatomic(g: Graph, src: int, dist, level_cap: int = 0, stats: bool = True, stream=None,
+                         expand_duplicates: bool = False):
+    """The paper's non-atomic top-down BFS (duplicates allowed); returns (totals or None, per-level list).
+    ``expand_duplicates`` expands every appended entry again (the paper's variant, BFS_DUP_EXPAND)."""
     st = bfs_dup_stats() if stats else None
     lv = (bfs_dup_level * level_cap)() if level_cap > 0 else None
-    _check(load().bfs_single_nonatomic(g.handle, int(src), _ptr(dist), ctypes.byref(st) if st is not None else None,
-                                       lv, level_cap, _stream_handle(stream)), "bfs_single_nonatomic")
+    mode = BFS_DUP_EXPAND if expand_duplicates else BFS_DUP_DEDUP
+    _check(load().bfs_single_nonatomic_ex(g.handle, int(src), _ptr(dist), mode,
+                                          ctypes.byref(st) if st is not None else None, lv, level_cap,
+                                          _stream_handle(stream)), "bfs_single_nonatomic")
     levels = [] if lv is None else [x.as_dict() for x in lv]
     if st is not None:
         levels = levels[:st.levels]

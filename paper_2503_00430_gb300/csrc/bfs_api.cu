@@ -497,15 +497,21 @@ int bfs_parents(bfs_graph* g, const int32_t* dist, int32_t* parent, void* stream
   return run_parents(g, dist, parent, reinterpret_cast<cudaStream_t>(stream));
 }
 
-int bfs_single_nonatomic(bfs_graph* g, int32_t src, int32_t* dist, bfs_dup_stats* stats, bfs_dup_level* levels,
-                         int32_t level_cap, void* stream) {
+int bfs_single_nonatomic_ex(bfs_graph* g, int32_t src, int32_t* dist, int mode, bfs_dup_stats* stats,
+                            bfs_dup_level* levels, int32_t level_cap, void* stream) {
   GBFS_NVTX("bfs_single_nonatomic");
   if (!g || !dist) return BFS_EINVAL;
   if (src < 0 || (int64_t)src >= g->n) return BFS_EINVAL;
+  if (mode != BFS_DUP_DEDUP && mode != BFS_DUP_EXPAND) return BFS_EINVAL;
   if (level_cap < 0 || (level_cap > 0 && !levels)) return BFS_EINVAL;
   if (!is_device_pointer(dist)) return BFS_EINVAL;
   std::lock_guard<std::mutex> lock(g->mu);
-  return run_nonatomic(g, src, dist, stats, levels, level_cap, reinterpret_cast<cudaStream_t>(stream));
+  return run_nonatomic(g, src, dist, mode, stats, levels, level_cap, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int bfs_single_nonatomic(bfs_graph* g, int32_t src, int32_t* dist, bfs_dup_stats* stats, bfs_dup_level* levels,
+                         int32_t level_cap, void* stream) {
+  return bfs_single_nonatomic_ex(g, src, dist, BFS_DUP_DEDUP, stats, levels, level_cap, stream);
 }
 
 int bfs_multi(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int dist_bits, void* stream) {

@@ -220,7 +220,7 @@ int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
                bfs_level_stat* levels, int level_cap, cudaStream_t stream);
-int run_nonatomic(bfs_graph* g, int src, int* dist, bfs_dup_stats* st, bfs_dup_level* lv, int lv_cap,
+int run_nonatomic(bfs_graph* g, int src, int* dist, int mode, bfs_dup_stats* st, bfs_dup_level* lv, int lv_cap,
                   cudaStream_t s);
 void free_nonatomic_ws(NonAtomicWs* ws);
 int ensure_multi_ws(bfs_graph* g, int ring);

@@ -35,7 +35,7 @@ struct MsCtrl {
   unsigned long long ntouch;    // push: touched vertices
   unsigned long long nheavy;    // pull: deferred high-degree vertices
   unsigned long long edges;     // entries examined (pull) or pushed (push)
-  unsigned long long pad;
+  unsigned long long active;    // pull: vertices still missing an active lane (their lists are read)
   unsigned long long act[4];    // lanes present in the new frontier
 };
 
@@ -577,7 +577,7 @@ template <int W, typename RP>
 __global__ void __launch_bounds__(256, GBFS_MS_PULL_MINB) k_ms_pull(MsArgs A) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
-  unsigned long long nf = 0, mf = 0, dd = 0, edges = 0;
+  unsigned long long nf = 0, mf = 0, dd = 0, edges = 0, nact = 0;
   Mask<W> act_acc;
 #pragma unroll
   for (int k = 0; k < W; ++k) act_acc.w[k] = 0;
@@ -592,6 +592,7 @@ __global__ void __launch_bounds__(256, GBFS_MS_PULL_MINB) k_ms_pull(MsArgs A) {
     if (v < A.n_live) {
       Mask<W> x = load_mask<W>(A.X + v * W);
       if (!covers<W>(x, A.act)) {
+        ++nact;
         const long long s = rpv<RP>(A.rp, v), e = rpv<RP>(A.rp, v + 1);
         if (e - s > A.heavy_min) {
           defer = true;
@@ -682,11 +683,13 @@ __global__ void __launch_bounds__(256, GBFS_MS_PULL_MINB) k_ms_pull(MsArgs A) {
   mf = warp_sum(mf);
   dd = warp_sum(dd);
   edges = warp_sum(edges);
+  nact = warp_sum(nact);
   if (ms_lane() == 0) {
     if (nf) atomicAdd(&A.ctrl->nf, nf);
     if (mf) atomicAdd(&A.ctrl->mf, mf);
     if (dd) atomicAdd(&A.ctrl->done_deg, dd);
     if (edges) atomicAdd(&A.ctrl->edges, edges);
+    if (nact) atomicAdd(&A.ctrl->active, nact);
   }
 }
 
@@ -1168,10 +1171,13 @@ int run_group(bfs_graph* g, const int* srcs, int lanes, T* dist, T unreached, in
       if (push) {
         ++st->push_levels;
         st->pushed_edges += (long long)c.edges;
+        st->push_frontier += nf;
       } else {
         ++st->pull_levels;
         st->pulled_edges += (long long)c.edges;
+        st->pull_active += (long long)c.active;
       }
+      st->found += (long long)c.nf;
     }
     for (int k = 0; k < 4; ++k) A.act[k] = c.act[k];
     nf_prev = nf;

@@ -9,16 +9,18 @@
 // per vertex: a bit-packed word written without atomics could lose bits and
 // change distances, a byte cannot.
 //
-// The paper expands duplicates again at the next level.  On this GPU a whole
-// level's tests run nearly at once, so a vertex with many frontier neighbours
-// is appended about once per neighbour, its copies re-read its list at the
-// next level, and duplicates multiply from level to level (they overflowed an
-// n + m entry queue on R-MAT scale 14 by the second level).  So between levels
-// the appended entries are reduced to distinct vertices without atomics: every
-// entry stores its index into owner[v] (plain 4-byte stores: one of them
-// remains), and the entry whose index remained is the one kept.  Per level the
-// library counts the appended entries (duplicates included), the distinct
-// vertices among them and the list entries read.
+// The paper expands duplicates again at the next level (mode BFS_DUP_EXPAND
+// here).  On this GPU a whole level's tests run nearly at once, so a vertex
+// with many frontier neighbours is appended about once per neighbour, its
+// copies re-read its list at the next level, and duplicates multiply from
+// level to level (they overflowed an n + m entry queue on R-MAT scale 14 by
+// the second level: BFS_ENOMEM, nothing written out of bounds).  So by default
+// (BFS_DUP_DEDUP) the appended entries are reduced between levels to distinct
+// vertices without atomics: every entry stores its index into owner[v] (plain
+// 4-byte stores: one of them remains), and the entry whose index remained is
+// the one kept.  Per level the library counts the appended entries
+// (duplicates included), the distinct vertices among them and the list
+// entries read.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -182,7 +184,8 @@ __global__ void k_na_own(const int* q, long long nq, int* owner) {
 }
 
 // Pass 2 (a later launch, so every store of pass 1 is visible): the entry
-// whose index remained is appended to the next frontier, once per vertex.
+// whose index remained is appended to the next frontier, once per vertex
+// (qnext null: the distinct vertices are only counted).
 __global__ void k_na_keep(const int* q, long long nq, const int* owner, int* qnext, unsigned long long* ctr) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
@@ -203,7 +206,7 @@ __global__ void k_na_keep(const int* q, long long nq, const int* owner, int* qne
     pos = __shfl_sync(0xffffffffu, pos, leader);
     unsigned lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    if (keep) qnext[pos + __popc(b & lt)] = v;
+    if (keep && qnext) qnext[pos + __popc(b & lt)] = v;
   }
 }
 
@@ -217,21 +220,26 @@ __global__ void k_na_init(unsigned char* vis, int* dist, long long n, int src, i
   if (tid == 0) q0[0] = src;
 }
 
+// One BFS.  expand_dups = false: a level expands the distinct vertices of the
+// appended entries; true (the paper's variant): it expands every appended
+// entry, duplicates included, which can outgrow the queues (BFS_ENOMEM).
 template <typename RP>
-int run_na(bfs_graph* g, NonAtomicWs& ws, int src, int* dist, bfs_dup_stats* st, bfs_dup_level* lv, int lv_cap,
-           cudaStream_t s) {
+int run_na(bfs_graph* g, NonAtomicWs& ws, int src, int* dist, bool expand_dups, bfs_dup_stats* st,
+           bfs_dup_level* lv, int lv_cap, cudaStream_t s) {
   const long long n = g->n;
   const int grid = g->num_sms * 8, block = 256;
-  k_na_init<<<grid, block, 0, s>>>(ws.vis, dist, n, src, ws.q[0]);
+  int* qin = ws.q[0];
+  int* qout = ws.q[1];
+  k_na_init<<<grid, block, 0, s>>>(ws.vis, dist, n, src, qin);
   GBFS_CUDA(cudaGetLastError());
-  long long nq = 1, appended = 1;  // the level-0 frontier {src}
+  long long nq = 1, appended = 1, uniq = 1;  // the level-0 frontier {src}
   int L = 0;
   for (;;) {
-    // Expand the distinct frontier q[0] into q[1] (duplicates possible) ...
+    // Expand the nq entries of qin into qout (duplicates possible) ...
     GBFS_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(unsigned long long) * C_COUNT, s));
-    k_na_level<RP><<<grid, block, 0, s>>>(g->rp, g->col, ws.q[0], nq, ws.q[1], ws.cap, ws.vis, dist, L, ws.heavy,
+    k_na_level<RP><<<grid, block, 0, s>>>(g->rp, g->col, qin, nq, qout, ws.cap, ws.vis, dist, L, ws.heavy,
                                           ws.hcap, ws.ctr);
-    k_na_chunks<RP><<<grid, block, 0, s>>>(g->rp, g->col, ws.q[1], ws.cap, ws.vis, dist, L, ws.heavy, ws.hcap,
+    k_na_chunks<RP><<<grid, block, 0, s>>>(g->rp, g->col, qout, ws.cap, ws.vis, dist, L, ws.heavy, ws.hcap,
                                            ws.ctr);
     GBFS_CUDA(cudaGetLastError());
     GBFS_CUDA(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(unsigned long long) * C_COUNT, cudaMemcpyDeviceToHost, s));
@@ -242,23 +250,32 @@ int run_na(bfs_graph* g, NonAtomicWs& ws, int src, int* dist, bfs_dup_stats* st,
     if (st) {
       st->levels = L + 1;
       st->frontier_entries += appended;
-      st->unique += nq;
+      st->unique += uniq;
       st->edges += edges;
     }
     if (lv && L < lv_cap) {
       lv[L].frontier = appended;
-      lv[L].unique = nq;
+      lv[L].unique = uniq;
       lv[L].edges = edges;
     }
     if (nout == 0) break;
-    // ... then reduce q[1] to distinct vertices in q[0].
-    k_na_own<<<grid, block, 0, s>>>(ws.q[1], nout, ws.owner);
-    k_na_keep<<<grid, block, 0, s>>>(ws.q[1], nout, ws.owner, ws.q[0], ws.ctr);
+    // ... then count the distinct vertices of qout, and keep them in qin (or
+    // keep every entry: the next level expands qout as it is).
+    k_na_own<<<grid, block, 0, s>>>(qout, nout, ws.owner);
+    k_na_keep<<<grid, block, 0, s>>>(qout, nout, ws.owner, expand_dups ? nullptr : qin, ws.ctr);
     GBFS_CUDA(cudaGetLastError());
     GBFS_CUDA(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(unsigned long long) * C_COUNT, cudaMemcpyDeviceToHost, s));
     GBFS_CUDA(cudaStreamSynchronize(s));
     appended = nout;
-    nq = (long long)ws.h_ctr[C_UNIQUE];
+    uniq = (long long)ws.h_ctr[C_UNIQUE];
+    if (expand_dups) {
+      int* t = qin;
+      qin = qout;
+      qout = t;
+      nq = nout;
+    } else {
+      nq = uniq;
+    }
     ++L;
   }
   return BFS_OK;
@@ -278,7 +295,7 @@ void free_nonatomic_ws(NonAtomicWs* ws) {
   delete ws;
 }
 
-int run_nonatomic(bfs_graph* g, int src, int* dist, bfs_dup_stats* st, bfs_dup_level* lv, int lv_cap,
+int run_nonatomic(bfs_graph* g, int src, int* dist, int mode, bfs_dup_stats* st, bfs_dup_level* lv, int lv_cap,
                   cudaStream_t s) {
   if (!g->na) {
     NonAtomicWs* ws = new NonAtomicWs();
@@ -308,8 +325,9 @@ int run_nonatomic(bfs_graph* g, int src, int* dist, bfs_dup_stats* st, bfs_dup_l
   }
   if (st) memset(st, 0, sizeof(*st));
   if (lv && lv_cap > 0) memset(lv, 0, sizeof(*lv) * (size_t)lv_cap);
-  return g->rp_bits == 32 ? run_na<int>(g, *g->na, src, dist, st, lv, lv_cap, s)
-                          : run_na<long long>(g, *g->na, src, dist, st, lv, lv_cap, s);
+  const bool expand = mode == BFS_DUP_EXPAND;
+  return g->rp_bits == 32 ? run_na<int>(g, *g->na, src, dist, expand, st, lv, lv_cap, s)
+                          : run_na<long long>(g, *g->na, src, dist, expand, st, lv, lv_cap, s);
 }
 
 }  // namespace gbfs

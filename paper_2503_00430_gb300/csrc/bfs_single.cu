@@ -25,6 +25,9 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <map>
+#include <mutex>
+
 #include "bfs_device.cuh"
 #include "bfs_internal.cuh"
 
@@ -1240,6 +1243,43 @@ static cudaError_t prepare_kernel(const void* fn, int threads_per_block) {
                               (int)dyn_smem_bytes(threads_per_block));
 }
 
+// Resident blocks per SM of a kernel at a block size (its shared-memory limit
+// set first), computed once per (device, kernel, block size): these queries
+// would otherwise run on the host before every launch, while the stream idles.
+static cudaError_t resident_blocks(const void* fn, int threads_per_block, int* per_sm) {
+  struct Key {
+    int dev;
+    const void* fn;
+    int threads;
+    bool operator<(const Key& o) const {
+      if (dev != o.dev) return dev < o.dev;
+      if (fn != o.fn) return fn < o.fn;
+      return threads < o.threads;
+    }
+  };
+  static std::mutex mu;
+  static std::map<Key, int> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const Key k{dev, fn, threads_per_block};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(k);
+    if (it != cache.end()) {
+      *per_sm = it->second;
+      return cudaSuccess;
+    }
+  }
+  e = prepare_kernel(fn, threads_per_block);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads_per_block, dyn_smem_bytes(threads_per_block));
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[k] = *per_sm;
+  return cudaSuccess;
+}
+
 static int resolve_policy(const bfs_graph* g, const bfs_params& p) {
   if (p.policy != BFS_POLICY_AUTO) return p.policy;
   // Section 3: average degree below 7 marks a large-diameter graph -> top-down only; several
@@ -1300,9 +1340,8 @@ template <typename RP, bool STATS>
 static int launch_persistent(bfs_graph* g, KParams& K, const bfs_params& p, cudaStream_t stream) {
   void* fn = Kernels<RP, STATS>::persistent();
   const size_t smem = dyn_smem_bytes(p.threads_per_block);
-  GBFS_CUDA(prepare_kernel(fn, p.threads_per_block));
   int per_sm = 0;
-  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, smem));
+  GBFS_CUDA(resident_blocks(fn, p.threads_per_block, &per_sm));
   if (per_sm < 1) return BFS_EINVAL;
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   dim3 grid((unsigned)(per_sm * g->num_sms)), block((unsigned)p.threads_per_block);
@@ -1417,9 +1456,8 @@ static int launch_graph(bfs_graph* g, KParams& K, const bfs_params& p, cudaStrea
   SingleWs& ws = g->ws;
   void* fn = Kernels<RP, false>::persistent();
   const size_t smem = dyn_smem_bytes(p.threads_per_block);
-  GBFS_CUDA(prepare_kernel(fn, p.threads_per_block));
   int per_sm = 0;
-  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p.threads_per_block, smem));
+  GBFS_CUDA(resident_blocks(fn, p.threads_per_block, &per_sm));
   if (per_sm < 1) return BFS_EINVAL;
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   cudaKernelNodeParams kp{};
@@ -1465,9 +1503,8 @@ int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads
                                cudaStream_t stream) {
   void* fn = rp_bits == 32 ? Kernels<int, false>::persistent() : Kernels<long long, false>::persistent();
   const size_t smem = dyn_smem_bytes(threads_per_block);
-  GBFS_CUDA(prepare_kernel(fn, threads_per_block));
   int per_sm = 0;
-  GBFS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads_per_block, smem));
+  GBFS_CUDA(resident_blocks(fn, threads_per_block, &per_sm));
   if (per_sm < 1) return BFS_EINVAL;
   dim3 grid((unsigned)(per_sm * num_sms)), block((unsigned)threads_per_block);
   void* args[] = {&K};

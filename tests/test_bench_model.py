@@ -79,3 +79,22 @@ def test_layout_bytes_row_pointers_no_queue():
     got = bench.layout_bytes(n, rp, LEVELS, head=False, queue=False)
     assert got == pytest.approx(query + l0 + l1 + l2)
     assert got == 657  # 400 + 50 + 103 + 104
+
+
+def test_msbfs_bytes_hand_worked():
+    """256 sources (W = 4 words, 32-byte masks), 8-byte row pointers, n = 100 vertices of which 80
+    have edges; one push level (2 frontier vertices, 10 pushed entries) and two pull levels
+    (50 + 20 vertices missing a lane, 300 + 40 entries examined); 60 vertices gained a lane in all;
+    uint8 output."""
+    st = dict(pull_levels=2, push_levels=1, pull_active=70, pulled_edges=340, push_frontier=2, pushed_edges=10,
+              found=60)
+    pull = 2 * (2 * 32 * 80) + 8 * 70 + (4 + 32) * 340        # masks of scanned vertices, row ptrs, gathers
+    push = (32 + 2 * 8) * 2 + (4 + 32) * 10                   # frontier masks + row ptrs, pushed entries
+    found = 2 * 32 * 60
+    out = 256 * 100 * 1
+    assert bench.msbfs_bytes(100, 80, 256, 8, st, 1) == pull + push + found + out
+    assert pull + push + found + out == 10240 + 560 + 12240 + 96 + 360 + 3840 + 25600
+    # 64 sources: one word (8-byte masks), int32 output
+    st1 = dict(st)
+    assert bench.msbfs_bytes(100, 80, 64, 4, st1, 4) == (2 * (2 * 8 * 80) + 4 * 70 + 12 * 340 + (8 + 8) * 2
+                                                         + 12 * 10 + 16 * 60 + 64 * 100 * 4)
