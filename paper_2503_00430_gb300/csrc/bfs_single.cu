@@ -27,6 +27,8 @@
 
 #include <map>
 #include <mutex>
+#include <tuple>
+#include <utility>
 
 #include "bfs_device.cuh"
 #include "bfs_internal.cuh"
@@ -1243,40 +1245,34 @@ static cudaError_t prepare_kernel(const void* fn, int threads_per_block) {
                               (int)dyn_smem_bytes(threads_per_block));
 }
 
-// Resident blocks per SM of a kernel at a block size (its shared-memory limit
-// set first), computed once per (device, kernel, block size): these queries
-// would otherwise run on the host before every launch, while the stream idles.
+// Resident blocks per SM of a kernel at a block size, with the kernel's
+// dynamic shared-memory limit set to what that block size uses.  The
+// occupancy is computed once per (device, kernel, block size) and the limit is
+// set only when it changes: these host calls would otherwise run before every
+// launch, while the stream idles.
 static cudaError_t resident_blocks(const void* fn, int threads_per_block, int* per_sm) {
-  struct Key {
-    int dev;
-    const void* fn;
-    int threads;
-    bool operator<(const Key& o) const {
-      if (dev != o.dev) return dev < o.dev;
-      if (fn != o.fn) return fn < o.fn;
-      return threads < o.threads;
-    }
-  };
   static std::mutex mu;
-  static std::map<Key, int> cache;
+  static std::map<std::tuple<int, const void*, int>, int> occ;   // (device, kernel, threads) -> blocks per SM
+  static std::map<std::pair<int, const void*>, int> limit;       // (device, kernel) -> shared-memory limit set
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const Key k{dev, fn, threads_per_block};
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(k);
-    if (it != cache.end()) {
-      *per_sm = it->second;
-      return cudaSuccess;
-    }
-  }
-  e = prepare_kernel(fn, threads_per_block);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads_per_block, dyn_smem_bytes(threads_per_block));
-  if (e != cudaSuccess) return e;
+  const int smem = (int)dyn_smem_bytes(threads_per_block);
   std::lock_guard<std::mutex> lock(mu);
-  cache[k] = *per_sm;
+  auto lit = limit.find({dev, fn});
+  if (lit == limit.end() || lit->second != smem) {
+    e = prepare_kernel(fn, threads_per_block);
+    if (e != cudaSuccess) return e;
+    limit[{dev, fn}] = smem;
+  }
+  auto it = occ.find({dev, fn, threads_per_block});
+  if (it != occ.end()) {
+    *per_sm = it->second;
+    return cudaSuccess;
+  }
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fn, threads_per_block, (size_t)smem);
+  if (e != cudaSuccess) return e;
+  occ[{dev, fn, threads_per_block}] = *per_sm;
   return cudaSuccess;
 }
 
