@@ -33,6 +33,17 @@ bool is_device_pointer(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory registered with CUDA (pinned),
+// through which kernels can store into it directly; null for pageable memory.
+void* pinned_device_alias(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 namespace {
 
 // Validation result bits.
@@ -455,6 +466,10 @@ int bfs_single_ex(bfs_graph* g, int32_t src, int32_t* dist, const bfs_params* pa
   }
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (is_device_pointer(dist)) return run_single(g, src, dist, p, stats, levels, level_cap, s);
+  // Pinned host output: the kernel stores the distances straight into it (the
+  // transfer to the host overlaps the final expansion instead of following it).
+  if (int* alias = static_cast<int*>(pinned_device_alias(dist)))
+    return run_single(g, src, alias, p, stats, levels, level_cap, s);
   SingleWs& ws = g->ws;
   if (!ws.dist_tmp) GBFS_CUDA(cudaMalloc(&ws.dist_tmp, sizeof(int) * (size_t)g->n));
   rc = run_single(g, src, ws.dist_tmp, p, stats, levels, level_cap, s);

@@ -210,6 +210,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
   } while (0)
 
 bool is_device_pointer(const void* p);
+void* pinned_device_alias(const void* p);
 int reorder_by_degree(bfs_graph* g);
 int build_head(bfs_graph* g);
 int vertices_by_degree(bfs_graph* g, int* order);

@@ -301,3 +301,18 @@ def test_frontier_rule_at_exactly_n_over_20(bfs, k, bottom_up):
         _, lv = bfs.bfs_single_ex(g, 0, d, params=bfs.make_params(policy=1, launch=launch), level_cap=8)
         assert lv[1]["frontier"] == k and lv[1]["direction"] == (1 if bottom_up else 0), (launch, lv[1])
     g.free()
+
+
+def test_pinned_host_output_written_directly(bfs):
+    """Pinned host output is written by the kernel through its device alias: exact on a hybrid
+    search, on the renumbered copy, and on a path deeper than 254 levels (where distances are
+    written during the levels instead of by the final expansion)."""
+    for (rp, col), kw in ((graphgen.rmat(14, seed=7), dict()), (graphgen.rmat(14, seed=7), dict(relabel=1)),
+                          (G.path_graph(600), dict(policy=3)), (G.path_graph(600), dict(policy=3, launch=1))):
+        g = bfs.bfs_graph_upload(rp, col)
+        n = len(rp) - 1
+        host = torch.full((n,), 77, dtype=torch.int32).pin_memory().numpy()
+        for src in (0, n // 3):
+            bfs.bfs_single_ex(g, src, host, params=bfs.make_params(**kw))
+            assert np.array_equal(host, oracle.bfs(rp, col, src)), (n, kw, src)
+        g.free()
