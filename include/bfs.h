@@ -289,8 +289,10 @@ int bfs_graph_info(const bfs_graph *g, int64_t *n, int64_t *m, int64_t *max_degr
  *  src    source vertex in [0, n).
  *  dist   int32[n], device or host memory (detected).  Device output is
  *         written in stream order; pinned (page-locked) host output is
- *         written by the kernel directly through its device alias; other host
- *         output is staged on the device and copied back before return.
+ *         written by the kernel directly through its device alias (except
+ *         under BFS_POLICY_LOCAL, whose atomic relaxations stay on the
+ *         device); other host output is staged on the device and copied back
+ *         before return.
  * Blocks until the query has finished (the device status word is read back).
  * Queries on one graph are serialized on the device (they share its workspace).
  * Errors: BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA, BFS_ETIMEOUT.

@@ -468,8 +468,10 @@ int bfs_single_ex(bfs_graph* g, int32_t src, int32_t* dist, const bfs_params* pa
   if (is_device_pointer(dist)) return run_single(g, src, dist, p, stats, levels, level_cap, s);
   // Pinned host output: the kernel stores the distances straight into it (the
   // transfer to the host overlaps the final expansion instead of following it).
-  if (int* alias = static_cast<int*>(pinned_device_alias(dist)))
-    return run_single(g, src, alias, p, stats, levels, level_cap, s);
+  // The multi-level local kernel relaxes distances with atomics: staged instead.
+  if (!uses_local_kernel(g, p))
+    if (int* alias = static_cast<int*>(pinned_device_alias(dist)))
+      return run_single(g, src, alias, p, stats, levels, level_cap, s);
   SingleWs& ws = g->ws;
   if (!ws.dist_tmp) GBFS_CUDA(cudaMalloc(&ws.dist_tmp, sizeof(int) * (size_t)g->n));
   rc = run_single(g, src, ws.dist_tmp, p, stats, levels, level_cap, s);

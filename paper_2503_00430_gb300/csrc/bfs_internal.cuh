@@ -211,6 +211,7 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
 bool is_device_pointer(const void* p);
 void* pinned_device_alias(const void* p);
+bool uses_local_kernel(const bfs_graph* g, const bfs_params& p);  // the query runs bfs_local.cu's kernel
 int reorder_by_degree(bfs_graph* g);
 int build_head(bfs_graph* g);
 int vertices_by_degree(bfs_graph* g, int* order);

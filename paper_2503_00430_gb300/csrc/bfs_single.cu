@@ -1286,6 +1286,8 @@ static int resolve_policy(const bfs_graph* g, const bfs_params& p) {
   return BFS_POLICY_EDGES;
 }
 
+bool uses_local_kernel(const bfs_graph* g, const bfs_params& p) { return resolve_policy(g, p) == BFS_POLICY_LOCAL; }
+
 static void fill_kparams(bfs_graph* g, int src, int* dist, const bfs_params& p, KParams& K) {
   SingleWs& ws = g->ws;
   const Relabel* rl = (p.relabel && g->rl && g->rl->h_new_of) ? g->rl : nullptr;

@@ -308,7 +308,8 @@ def test_pinned_host_output_written_directly(bfs):
     search, on the renumbered copy, and on a path deeper than 254 levels (where distances are
     written during the levels instead of by the final expansion)."""
     for (rp, col), kw in ((graphgen.rmat(14, seed=7), dict()), (graphgen.rmat(14, seed=7), dict(relabel=1)),
-                          (G.path_graph(600), dict(policy=3)), (G.path_graph(600), dict(policy=3, launch=1))):
+                          (G.path_graph(600), dict(policy=3)), (G.path_graph(600), dict(policy=3, launch=1)),
+                          (G.path_graph(600), dict())):  # AUTO: the local kernel, staged
         g = bfs.bfs_graph_upload(rp, col)
         n = len(rp) - 1
         host = torch.full((n,), 77, dtype=torch.int32).pin_memory().numpy()
