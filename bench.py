@@ -49,9 +49,10 @@ def peaks():
 
 
 def measured_traffic():
-    """(mean per-launch DRAM traffic, indices of the captured sources) of the
-    persistent kernel from the committed ncu record, or None when the kernel's
-    sources changed since it was captured."""
+    """DRAM traffic per launch of the persistent kernel over its compulsory bytes (algorithmic_bytes),
+    from the committed ncu record: captured on the small case of the same kernel (R-MAT scale 23,
+    the headline's parameters), where traffic and compulsory bytes are both per launch of the same
+    sources.  None when the kernel's sources changed since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "bfs_persistent_traffic.json")) as f:
@@ -62,7 +63,7 @@ def measured_traffic():
                 h.update(f.read())
         if h.hexdigest() != rec["source_sha256"]:
             return None
-        return float(rec["traffic_bytes_per_launch_s25"]), list(rec.get("source_indices", []))
+        return float(rec["traffic_over_algorithmic"]), rec["captured_case"]
     except Exception:
         return None
 
@@ -104,6 +105,11 @@ def query_params(bfs, args, n=0, m=0):
         v = getattr(args, k)
         if v is not None:
             setattr(p, k, v)
+    for kv in args.set or []:
+        k, v = kv.split("=", 1)
+        if not hasattr(p, k):
+            raise SystemExit(f"--set: bfs_params has no field {k}")
+        setattr(p, k, int(v))
     return p
 
 
@@ -119,6 +125,8 @@ def parse_args(argv=None):
     ap.add_argument("--relabel", type=int, default=None, choices=[0, 1],
                     help="single-source queries on the degree-renumbered copy of the graph (default: tuning table)")
     ap.add_argument("--no-tuned", action="store_true", help="library defaults instead of the tuning table")
+    ap.add_argument("--set", action="append", metavar="FIELD=VALUE",
+                    help="single-source workloads: override one bfs_params field (repeatable)")
     ap.add_argument("--tune-out", default=None, help="tune: table to write (default: the package's tuned.json)")
     ap.add_argument("--cpu-sample", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -208,6 +216,12 @@ def msbfs_bytes(n, n_live, lanes, rp_bytes, st, out_bytes_per_entry):
     b += (mb + 2 * rp_bytes) * st["push_frontier"] + (4 + mb) * st["pushed_edges"]
     b += 2 * mb * st["found"]
     return b + lanes * n * out_bytes_per_entry
+
+
+def graphset_bytes(vertices, entries, graphs):
+    """Bytes of one graph-set launch: every graph's int64 row pointers (n_i + 1 each) and int32
+    lists read once, its int32 distances written once (its bitmaps live in shared memory)."""
+    return 8 * (vertices + graphs) + 4 * entries + 4 * vertices
 
 
 def layout_bytes(n, rp_bytes, levels, head=True, queue=True):
@@ -435,17 +449,16 @@ def run_ours(args):
     lat = np.array(secs) * 1e3
     hbm, peak_kind = peaks()
     achieved = float(np.sum(byts) / np.sum(secs) / 1e9)
-    # DRAM traffic of the same kernel from the committed ncu record (captured on
-    # this workload), and its ratio to the algorithmic bytes of the captured sources.
-    traffic, traffic_ratio = None, None
+    # DRAM traffic of the same kernel from the committed ncu record: the ratio of traffic to
+    # compulsory bytes measured on the small case, applied to this workload's compulsory bytes.
+    traffic, traffic_ratio, traffic_case = None, None, None
     default_run = (args.scale == SCALE and args.workload == "rmat25" and not args.no_degree_order
-                   and args.policy is None and args.launch is None and args.relabel is None and not args.no_tuned)
+                   and args.policy is None and args.launch is None and args.relabel is None and not args.no_tuned
+                   and not args.set)
     mt = measured_traffic() if default_run else None
     if mt is not None:
-        traffic = mt[0]
-        idx = [i for i in mt[1] if i < len(per_src)]
-        if idx:
-            traffic_ratio = traffic / float(np.mean([per_src[i]["bytes"] for i in idx]))
+        traffic_ratio, traffic_case = mt
+        traffic = traffic_ratio * float(np.mean([p["bytes"] for p in per_src]))
 
     # End to end through the C ABI with a pinned host output buffer (D2H copy inside).
     host_out = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
@@ -495,6 +508,9 @@ def run_ours(args):
                      "peak_kind": peak_kind,
                      "traffic": traffic,
                      "traffic_vs_algorithmic": traffic_ratio,
+                     "traffic_source": None if traffic is None else
+                     f"ncu dram__bytes_read+write per launch on {traffic_case}, as a ratio to the compulsory "
+                     "bytes of the captured launches, times this workload's mean compulsory bytes",
                      "kernel": "bfs_persistent_kernel<long long,false> (one launch per BFS)",
                      "bytes_per_bfs_mean": float(np.mean([p["bytes"] for p in per_src])),
                      "bytes_model": "compulsory bytes of the method (init 4n+n/8; top-down 4F+2RP*F+4E+8F'; "
@@ -717,11 +733,19 @@ def run_graphset(args):
         tot += a.elapsed_time(b) / 1e3
         k += 1
         g.free()
+    # Bytes of one launch: every graph's row pointers (8 bytes each) and lists (4 bytes per entry)
+    # read once and its distances written once; the bitmaps live in shared memory.
+    byts = graphset_bytes(int(gs.voff[-1]), int(gs.eoff[-1]), count)
+    hbm, peak_kind = peaks()
     _json({"metric": "graphs/s, one launch over a set of small graphs", "value": count / t, "unit": "graphs/s",
            "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
            "config": {"workload": f"graphset_{count}_er_1e3_1e5_d8", "vertices": int(gs.voff[-1]),
                       "entries": int(gs.eoff[-1]), "ms_per_launch": t * 1e3, "stats": st,
-                      "single_source_graphs_per_s": k / tot, "vs_single_source": (count / t) / (k / tot)}})
+                      "single_source_graphs_per_s": k / tot, "vs_single_source": (count / t) / (k / tot),
+                      "roofline": {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm, "unit": "GB/s",
+                                   "frac": byts / t / 1e9 / hbm, "peak_kind": peak_kind, "bytes_per_launch": byts,
+                                   "bytes_model": "CSR read once (8 B per row pointer, 4 B per entry) + int32 "
+                                                  "distances written once", "kernel": "k_graphset"}}})
     return 0
 
 
@@ -817,6 +841,34 @@ def run_serve(args):
     run_rate(float("inf"), 256)  # warm-up: creates the groups
     sat = run_rate(float("inf"), args.serve_queries)
     cap = sat["achieved_qps"]
+    # Per graph: served capacity of that graph's queries alone against its sequential queries.
+    per_graph = {}
+    for gi, (name, n) in enumerate(graphs):
+        seq = [(gi, int(srcpool[gi][j])) for j in range(32)]
+        for _, sv in seq[:2]:
+            bfs.bfs_single(handles[gi], sv, d[gi])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _, sv in seq:
+            bfs.bfs_single(handles[gi], sv, d[gi])
+        torch.cuda.synchronize()
+        seq_g = len(seq) / (time.perf_counter() - t0)
+        nq = 640
+        qs_g = [(gi, int(srcpool[gi][j % 4096])) for j in range(nq)]
+        start = time.monotonic_ns()
+        tick = []
+        free_b = list(range(pool))
+        for _, sv in qs_g:
+            if not free_b:  # recycle the oldest query's buffer once it is done
+                tk, b_done = tick.pop(0)
+                srv.wait(tk)
+                free_b.append(b_done)
+            b = free_b.pop()
+            tick.append((srv.submit(ids[gi], sv, bufs[gi][b]), b))
+        for tk, _ in tick:
+            srv.wait(tk)
+        served = nq / ((time.monotonic_ns() - start) / 1e9)
+        per_graph[name] = {"served_qps": served, "sequential_qps": seq_g, "vs_sequential": served / seq_g}
     rates = {}
     for f in (0.1, 0.3, 0.5, 0.7, 0.9, 1.2):
         rates[str(f)] = run_rate(f * cap, args.serve_queries)
@@ -825,7 +877,7 @@ def run_serve(args):
            "unit": "queries/s", "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
            "config": {"workload": "serve_5graphs_poisson", "graphs": [g[0] for g in graphs],
                       "saturated": sat, "sequential_single_source_qps": seq_qps, "vs_sequential": cap / seq_qps,
-                      "rates": rates}})
+                      "per_graph_alone": per_graph, "rates": rates}})
     return 0
 
 

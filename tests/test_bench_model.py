@@ -98,3 +98,8 @@ def test_msbfs_bytes_hand_worked():
     st1 = dict(st)
     assert bench.msbfs_bytes(100, 80, 64, 4, st1, 4) == (2 * (2 * 8 * 80) + 4 * 70 + 12 * 340 + (8 + 8) * 2
                                                          + 12 * 10 + 16 * 60 + 64 * 100 * 4)
+
+
+def test_graphset_bytes():
+    # 3 graphs, 10 vertices, 40 entries: 8 * (10 + 3) row pointers + 4 * 40 list + 4 * 10 distances
+    assert bench.graphset_bytes(10, 40, 3) == 104 + 160 + 40
