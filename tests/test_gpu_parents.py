@@ -108,3 +108,31 @@ def test_invalid(bfs):
         bfs.bfs_parents(g, d, np.zeros(4, dtype=np.int32))
     assert e.value.code == bfs.BFS_EINVAL
     g.free()
+
+
+def test_calls_on_two_streams_share_the_workspace_safely(bfs):
+    """Parent arrays of one graph requested on two streams back to back: the calls share the
+    graph's workspace for long lists (more than 1056 entries: chunk records), and the library orders
+    them on the device, so both results follow the rule exactly."""
+    # Two hubs whose lists are longer than 1056 entries, joined by a path; leaves hang off both.
+    n = 6000
+    edges = [(0, i) for i in range(2, 3000)] + [(1, i) for i in range(2500, 6000)] + [(0, 5999)]
+    rp, col = G.csr_from_edges(n, edges)
+    assert np.diff(rp).max() > 1056
+    g = bfs.bfs_graph_upload(rp, col)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    srcs = (2, 4000)
+    dists = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in srcs]
+    for d, s_ in zip(dists, srcs):
+        bfs.bfs_single(g, s_, d)
+    torch.cuda.synchronize()
+    for rep in range(3):
+        pars = [torch.full((n,), 77, dtype=torch.int32, device="cuda") for _ in srcs]
+        torch.cuda.synchronize()
+        bfs.bfs_parents(g, dists[0], pars[0], stream=s1)
+        bfs.bfs_parents(g, dists[1], pars[1], stream=s2)
+        torch.cuda.synchronize()
+        for d, p in zip(dists, pars):
+            dd = d.cpu().numpy()
+            assert np.array_equal(p.cpu().numpy(), first_rule(rp, col, dd)), rep
+    g.free()
