@@ -137,3 +137,26 @@ def test_invalid(bfs):
             bfs.bfs_multi(g, np.array(srcs, dtype=np.int32), out, dist_bits=bits)
         assert e.value.code == bfs.BFS_EINVAL
     g.free()
+
+
+def test_counters_against_the_oracle_rows(bfs):
+    """The call's counters against facts of its exact output (one group of 256 sources): every
+    vertex that a lane reaches (other than at its own source) gains that lane at some level, so
+    `found` lies between the most vertices one lane reaches and the sum over lanes; a pull level
+    reads at most every vertex of degree > 0, a push level's frontier at most every vertex; the
+    output is written once per row."""
+    rp, col = graphgen.rmat(13, seed=22)
+    n = len(rp) - 1
+    g = bfs.bfs_graph_upload(rp, col)
+    srcs = graphgen.sources(rp, 256, 2300)
+    got, st = run_multi(bfs, g, n, srcs, 32)
+    want = oracle.bfs_many(rp, col, srcs)
+    assert np.array_equal(got, want)
+    reached = (want >= 0).sum(axis=1)
+    live = int((np.diff(rp) > 0).sum())
+    assert reached.max() - 1 <= st["found"] <= int(reached.sum())
+    assert 0 < st["pull_active"] <= st["pull_levels"] * live
+    assert st["push_frontier"] <= st["push_levels"] * n and st["push_frontier"] >= (st["push_levels"] > 0)
+    assert st["output_bytes"] >= 4 * 256 * n
+    assert st["push_levels"] + st["pull_levels"] >= int(want.max()) + 1
+    g.free()
