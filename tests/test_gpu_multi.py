@@ -155,7 +155,7 @@ def test_counters_against_the_oracle_rows(bfs):
     reached = (want >= 0).sum(axis=1)
     live = int((np.diff(rp) > 0).sum())
     assert reached.max() - 1 <= st["found"] <= int(reached.sum())
-    assert 0 < st["pull_active"] <= st["pull_levels"] * live
+    assert st["pull_active"] <= st["pull_levels"] * live and (st["pull_levels"] == 0 or st["pull_active"] > 0)
     assert st["push_frontier"] <= st["push_levels"] * n and st["push_frontier"] >= (st["push_levels"] > 0)
     assert st["output_bytes"] >= 4 * 256 * n
     assert st["push_levels"] + st["pull_levels"] >= int(want.max()) + 1
