@@ -655,6 +655,18 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
 __device__ __forceinline__ void round_vertices(unsigned act, int excl, int total, long long w0, int r0,
                                                int (&v)[kBuU]) {
   const unsigned lane = lane_id();
+  if (total > 32 * 32 - 32) {
+    // Nearly every vertex of the batch is unvisited: packing would give the
+    // same 32 rounds, so round r takes word r as it is (lane i = bit i; -1
+    // where the vertex is visited) and skips the search for each lane's vertex.
+#pragma unroll
+    for (int k = 0; k < kBuU; ++k) {
+      const int wi = r0 / 32 + k;
+      const unsigned aw = __shfl_sync(kFull, act, wi & 31);
+      v[k] = (wi < 32 && ((aw >> lane) & 1u)) ? (int)((w0 + wi) * 32 + (long long)lane) : -1;
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < kBuU; ++k) {
     const int kk = r0 + 32 * k + (int)lane;
@@ -761,24 +773,43 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
         pw0[k] = nw0[k];
         pw1[k] = nw1[k];
       }
+      // The warp's pending queue and new-frontier words are its own: deferred
+      // vertices take slots by a ballot prefix count, and in a dense batch
+      // (round r = word r) the round's found vertices are word r's new bits.
+      const bool dense = total > 32 * 32 - 32;
+      int np = sm.npend;
 #pragma unroll
       for (int k = 0; k < kBuU; ++k) {
-        if (v[k] < 0) continue;
         const int d = hd[k].w;
-        if (f0[k] | f1[k]) {
+        const bool fnd = v[k] >= 0 && (f0[k] | f1[k]);
+        const bool enq = v[k] >= 0 && !(f0[k] | f1[k]) && d > 2;
+        const unsigned em = __ballot_sync(kFull, enq);
+        if (dense) {
+          const unsigned fm = __ballot_sync(kFull, fnd);
+          if (lane == 0 && fm) sm.next[(r0 >> 5) + k] |= fm;
+          if (fnd) {
+            mark_level(P, direct, v[k], L);
+            acc.found += 1;
+            acc.mf += (unsigned long long)d;
+          }
+        } else if (fnd) {
           bu_mark_found(P, L, direct, sm, w0, v[k], d, acc);
-          if (STATS) acc.edges += f0[k] ? 1ull : 2ull;
-        } else if (d > 2) {
-          const int slot = atomicAdd(&sm.npend, 1);
+        }
+        if (STATS && fnd) acc.edges += f0[k] ? 1ull : 2ull;
+        if (enq) {
+          const int slot = np + __popc(em & lanemask_lt());
           sm.pstart[slot] = (long long)hd[k].z + 2;
           sm.plen[slot] = d - 2;
           sm.pv[slot] = v[k];
           sm.pd[slot] = d;
           sm.pex[slot] = 2;
-        } else if (STATS) {
+        } else if (STATS && v[k] >= 0 && !fnd) {
           acc.edges += (unsigned long long)d;
         }
+        np += __popc(em);
       }
+      __syncwarp();
+      if (lane == 0) sm.npend = np;
     } else {
       round_vertices(act, excl, total, w0, r0, v);
       long long s[kBuU], e[kBuU];
