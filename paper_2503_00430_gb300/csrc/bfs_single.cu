@@ -178,43 +178,70 @@ __device__ __noinline__ void init_phase(const KParams& P) {
 // dist[v] = level byte of v, or -1 where it is 255 (every vertex written).
 // On a renumbered graph the byte of caller vertex v is at new_of[v]; a
 // vertex of degree 0 (new id >= n_live) other than the source is unreached.
+// Each thread takes kExpandBatch groups of four vertices at once (all loads
+// issued before the first use), so that a thread has several stream loads and
+// level-byte gathers in flight instead of one dependent chain per group.
+constexpr int kExpandBatch = 4;
+
 __device__ __noinline__ void expand_phase(const KParams& P) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long n = P.n;
   long long done = 0;
   if (P.new_of) {
-    auto level_of = [&](int nv) -> int {
-      if ((long long)nv >= P.n_live && nv != P.src) return -1;
-      const int t = P.lv8[BV(nv, 6)];
+    auto level_at = [&](int nv) -> int {
+      const bool live = (long long)nv < P.n_live || nv == P.src;
+      const int t = live ? (int)P.lv8[BV(nv, 6)] : 255;
       return t == 255 ? -1 : t;
     };
     if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
       const long long n4 = n >> 2;
       const int4* m4 = reinterpret_cast<const int4*>(P.new_of);
       int4* d4 = reinterpret_cast<int4*>(P.dist);
-      for (long long i = tid; i < n4; i += nth) {
-        const int4 a = __ldcs(m4 + i);
-        __stcs(d4 + i, make_int4(level_of(a.x), level_of(a.y), level_of(a.z), level_of(a.w)));
+      for (long long i0 = tid; i0 < n4; i0 += nth * kExpandBatch) {
+        int4 a[kExpandBatch];
+#pragma unroll
+        for (int u = 0; u < kExpandBatch; ++u) {
+          const long long i = i0 + u * nth;
+          a[u] = i < n4 ? __ldcs(m4 + i) : make_int4(0, 0, 0, 0);
+        }
+        int4 r[kExpandBatch];
+#pragma unroll
+        for (int u = 0; u < kExpandBatch; ++u)
+          r[u] = make_int4(level_at(a[u].x), level_at(a[u].y), level_at(a[u].z), level_at(a[u].w));
+#pragma unroll
+        for (int u = 0; u < kExpandBatch; ++u) {
+          const long long i = i0 + u * nth;
+          if (i < n4) __stcs(d4 + i, r[u]);
+        }
       }
       done = n4 << 2;
     }
-    for (long long i = done + tid; i < n; i += nth) P.dist[i] = level_of(P.new_of[BV(i, 7)]);
+    for (long long i = done + tid; i < n; i += nth) P.dist[i] = level_at(P.new_of[BV(i, 7)]);
     return;
   }
   if ((reinterpret_cast<uintptr_t>(P.dist) & 15u) == 0) {
     const long long n4 = n >> 2;
     const unsigned* l4 = reinterpret_cast<const unsigned*>(P.lv8);
     int4* d4 = reinterpret_cast<int4*>(P.dist);
-    for (long long i = tid; i < n4; i += nth) {
-      const unsigned b = l4[i];
-      int x[4];
+    for (long long i0 = tid; i0 < n4; i0 += nth * kExpandBatch) {
+      unsigned b[kExpandBatch];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int t = (int)((b >> (8 * k)) & 0xffu);
-        x[k] = t == 255 ? -1 : t;
+      for (int u = 0; u < kExpandBatch; ++u) {
+        const long long i = i0 + u * nth;
+        b[u] = i < n4 ? l4[i] : 0u;
       }
-      __stcs(d4 + i, make_int4(x[0], x[1], x[2], x[3]));
+#pragma unroll
+      for (int u = 0; u < kExpandBatch; ++u) {
+        const long long i = i0 + u * nth;
+        int x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int t = (int)((b[u] >> (8 * k)) & 0xffu);
+          x[k] = t == 255 ? -1 : t;
+        }
+        if (i < n4) __stcs(d4 + i, make_int4(x[0], x[1], x[2], x[3]));
+      }
     }
     done = n4 << 2;
   }
