@@ -904,16 +904,26 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
   __syncwarp();
 }
 
+// Bitmap words that can hold a vertex of degree > 0: on a renumbered copy the
+// words of ids below n_live, else every word.  Degree-0 vertices are set in the
+// visited mask from the start and are no vertex's neighbour, so bottom-up
+// levels and conversions never need the words past these: the frontier bits
+// there are neither written nor read.
+__device__ __forceinline__ long long live_words(const KParams& P) {
+  const long long lw = P.new_of ? (P.n_live + 31) >> 5 : (long long)P.nw;
+  return lw < (long long)P.nw ? lw : (long long)P.nw;
+}
+
 // Visited word of lane `lane` in the batch starting at word w0 (all-set past the end).
 __device__ __forceinline__ unsigned batch_word(const KParams& P, long long w0) {
   const long long w = w0 + lane_id();
   return w < P.nw ? P.vis[BW(w, 48)] : kFull;
 }
 
-// Bottom-up level.  Batches of 32 words go to warps statically (interleaved:
-// bu_chunk = 0, or a level with fewer unvisited vertices than bitmap words,
-// where most batches are empty and a shared cursor would only add atomics) or
-// bu_chunk batches at a time from a shared cursor.  A warp requests its next
+// Bottom-up level, over the live words.  Batches of 32 words go to warps
+// statically (interleaved: bu_chunk = 0, or a level with fewer unvisited
+// vertices than bitmap words, where most batches are empty and a shared cursor
+// would only add atomics) or bu_chunk batches at a time from a shared cursor.  A warp requests its next
 // grab (and loads the visited words of its next batch) before it processes
 // the current batch, so neither latency sits between two batches.
 template <typename RP, bool STATS>
@@ -922,7 +932,7 @@ __device__ void bu_phase(const KParams& P, int L, bool direct, const unsigned* f
   BuWarpSmem& sm = reinterpret_cast<BuWarpSmem*>(g_dyn_smem)[threadIdx.x >> 5];
   Slot* out = &P.ctrl->slot[(L + 1) & 3];
   const unsigned lane = lane_id();
-  const long long nbatch = ((long long)P.nw + 31) / 32;
+  const long long nbatch = (live_words(P) + 31) / 32;
   if (lane == 0) sm.npend = 0;
   __syncwarp();
   Acc acc;
@@ -1001,14 +1011,15 @@ __device__ __noinline__ void convert_phase(const KParams& P, int L, const unsign
   const long long gw = (long long)blockIdx.x + (long long)gridDim.x * (threadIdx.x >> 5);
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   constexpr int kW = 8;  // bitmap words per lane: 8192 vertices per warp step (frontiers here are sparse)
-  const long long nstep = ((long long)P.nw + 32 * kW - 1) / (32 * kW);
+  const long long nwl = live_words(P);
+  const long long nstep = (nwl + 32 * kW - 1) / (32 * kW);
   for (long long bt = gw; bt < nstep; bt += nwarps) {
     const long long w0 = bt * 32 * kW + (long long)lane * kW;
     unsigned x[kW];
     int cnt = 0;
 #pragma unroll
     for (int j = 0; j < kW; ++j) {
-      x[j] = w0 + j < P.nw ? fbm[w0 + j] : 0u;
+      x[j] = w0 + j < nwl ? fbm[w0 + j] : 0u;
       cnt += __popc(x[j]);
     }
     const int incl = warp_incl_scan(cnt);
