@@ -55,14 +55,16 @@ static __device__ __forceinline__ void cp_async_wait() {
 // L2 eviction-priority policies: data read once per level (adjacency, head
 // records) is marked evict-first, the small per-vertex state that every level
 // updates (level bytes) evict-last, so the streaming reads do not push it out.
+// A policy is a plain value (no side effect), so the compiler may compute it
+// once outside a loop.
 static __device__ __forceinline__ unsigned long long policy_evict_first() {
   unsigned long long pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
 static __device__ __forceinline__ unsigned long long policy_evict_last() {
   unsigned long long pol;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
   return pol;
 }
 static __device__ __forceinline__ void st_u8_last(unsigned char* p, unsigned v) {

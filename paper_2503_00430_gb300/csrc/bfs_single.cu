@@ -501,20 +501,13 @@ __device__ void td_phase(const KParams& P, int L, bool direct, unsigned long lon
 #define in_frontier(front, u) ((((front)[BWF((u) >> 5, 26)]) >> ((u) & 31)) & 1u)
 
 // Shared-memory staging of one warp in a bottom-up batch.
-#ifndef GBFS_BU_U
-#define GBFS_BU_U 1
-#endif
 #ifndef GBFS_DRAIN_MIN
 #define GBFS_DRAIN_MIN 32
 #endif
-constexpr int kBuU = GBFS_BU_U;       // unvisited vertices per lane in flight in a bottom-up round
+constexpr int kBuU = 1;  // unvisited vertices per lane in a bottom-up round
 constexpr int kDrainMin = GBFS_DRAIN_MIN;  // deferred scans that trigger a drain within a batch
 constexpr int kPendCap = 32 * kBuU + kDrainMin - 1;  // deferred long scans per warp
-#ifndef GBFS_BU_DEPTH
-#define GBFS_BU_DEPTH 2
-#endif
-constexpr int kDepth = GBFS_BU_DEPTH;  // bottom-up rounds whose head records are in flight ahead of use
-constexpr int kNBuf = kDepth + 1;
+constexpr int kNBuf = 3;  // ring slots of head records in flight
 struct BuWarpSmem {
   int4 hbuf[kNBuf][32 * kBuU];   // head records of the rounds in flight (lane-private slots)
   int vbuf[kNBuf][32 * kBuU];    // their vertices
@@ -705,40 +698,127 @@ __device__ __forceinline__ void round_vertices(unsigned act, int excl, int total
   }
 }
 
-// Warp-collective: request the head records of round r of a batch into
-// buffer b (a zero-filled slot for lanes past the end, vertex -1).
-__device__ __forceinline__ void bu_issue_round(const KParams& P, BuWarpSmem& sm, unsigned act, int excl, int total,
-                                               long long w0, int r, int b) {
-  const unsigned lane = lane_id();
-  int v[kBuU];
-  round_vertices(act, excl, total, w0, r * 32 * kBuU, v);
-#pragma unroll
-  for (int k = 0; k < kBuU; ++k) {
-    sm.vbuf[b][32 * k + lane] = v[k];
-    cp_async16_first(&sm.hbuf[b][32 * k + lane], v[k] >= 0 ? P.head + BV(v[k], 33) : P.head, v[k] >= 0 ? 16 : 0);
-  }
-}
+#ifndef GBFS_BU_HEAD_DEPTH
+#define GBFS_BU_HEAD_DEPTH 2
+#endif
+constexpr int kHeadDepth = GBFS_BU_HEAD_DEPTH;  // rounds of head records in flight (2 or 3)
 
-// Frontier words holding the two head neighbours of this lane's vertices in
-// round buffer b (0 where a neighbour is missing or the slot is empty).
-__device__ __forceinline__ void bu_probe_words(const KParams& P, const BuWarpSmem& sm, const unsigned* front, int b,
-                                               unsigned (&w0)[kBuU], unsigned (&w1)[kBuU]) {
+// Warp-collective: the rounds of a batch on the head table.  A dense batch
+// (nearly every vertex unvisited) takes word r as round r, lane i its bit i;
+// otherwise the unvisited vertices are packed onto the lanes
+// (round_vertices).  An idle lane (-1) gets a zero-filled head record: degree
+// 0, which no unvisited vertex has (degree-0 vertices are visited from the
+// start).  Pipeline: round r + kHeadDepth's records are requested, round
+// r + 1's frontier words are loaded (its record and vertex are then kept in
+// registers, which frees the ring slot), round r is decided.  Deferred scans
+// are drained here once kDrainMin are pending; the rest are left in sm.npend.
+template <bool STATS>
+__device__ __forceinline__ void bu_head_batch(const KParams& P, int L, bool direct, const unsigned* front,
+                                              long long w0, unsigned act, int excl, int total, BuWarpSmem& sm,
+                                              Acc& acc) {
+  static_assert(kNBuf == 3 && kBuU == 1 && (kHeadDepth == 2 || kHeadDepth == 3), "head pipeline layout");
   const unsigned lane = lane_id();
+  const bool dense = total > 32 * 32 - 32;
+  const int nrounds = dense ? 32 : (total + 31) / 32;
+  auto issue = [&](int r, int b) {
+    int v;
+    if (dense) {
+      v = (__shfl_sync(kFull, act, r) >> lane) & 1u ? (int)((w0 + r) * 32 + (long long)lane) : -1;
+    } else {
+      int vv[1];
+      round_vertices(act, excl, total, w0, 32 * r, vv);
+      v = vv[0];
+    }
+    sm.vbuf[b][lane] = v;
+    cp_async16_first(&sm.hbuf[b][lane], v >= 0 ? P.head + BV(v, 33) : P.head, v >= 0 ? 16 : 0);
+  };
+  auto probe = [&](int b, int4& h, int& v, unsigned& x0, unsigned& x1) {
+    h = sm.hbuf[b][lane];
+    v = sm.vbuf[b][lane];
+    x0 = h.w > 0 ? front[BWF(h.x >> 5, 34)] : 0u;  // a vertex of degree > 0 has a first neighbour
+    x1 = h.w > 0 && h.y >= 0 ? front[BWF(h.y >> 5, 35)] : 0u;
+  };
 #pragma unroll
-  for (int k = 0; k < kBuU; ++k) {
-    const int4 h = sm.vbuf[b][32 * k + lane] >= 0 ? sm.hbuf[b][32 * k + lane] : make_int4(-1, -1, 0, 0);
-    w0[k] = h.x >= 0 ? front[BWF(h.x >> 5, 34)] : 0u;
-    w1[k] = h.y >= 0 ? front[BWF(h.y >> 5, 35)] : 0u;
+  for (int r = 0; r < kHeadDepth; ++r) {
+    if (r < nrounds) issue(r, r);
+    cp_async_commit();
   }
+  int4 h = make_int4(0, 0, 0, 0);
+  int v = -1;
+  unsigned p0 = 0, p1 = 0;
+  if (nrounds > 0) {
+    cp_async_wait<kHeadDepth - 1>();
+    probe(0, h, v, p0, p1);
+  }
+  int np = 0;  // deferred scans pending (sm.npend is written before a drain)
+  int bi = kHeadDepth % 3, bp = 1;  // ring slots of the round to request and of the round to probe
+#pragma unroll 1
+  for (int r = 0; r < nrounds; ++r) {
+    if (r + kHeadDepth < nrounds) issue(r + kHeadDepth, bi);
+    cp_async_commit();
+    bi = bi == 2 ? 0 : bi + 1;
+    int4 hn = make_int4(0, 0, 0, 0);
+    int vn = -1;
+    unsigned n0 = 0, n1 = 0;
+    if (r + 1 < nrounds) {
+      cp_async_wait<kHeadDepth - 1>();
+      probe(bp, hn, vn, n0, n1);
+    }
+    bp = bp == 2 ? 0 : bp + 1;
+    // Decide round r: p0/p1 are 0 for idle lanes and a missing second
+    // neighbour (id -1), so no bit of them is found there.
+    const int d = h.w;
+    const unsigned f0 = (p0 >> (h.x & 31)) & 1u, f1 = (p1 >> (h.y & 31)) & 1u;
+    const bool fnd = (f0 | f1) != 0u;
+    const bool enq = !fnd && d > 2;
+    if (dense) {
+      const unsigned fm = __ballot_sync(kFull, fnd);
+      if (lane == 0) sm.next[r] = fm;  // word r is this round's alone until the drains
+    } else if (fnd) {
+      atomicOr(&sm.next[(int)((long long)v / 32 - w0)], 1u << (v & 31));
+    }
+    if (fnd) {
+      mark_level(P, direct, v, L);
+      acc.found += 1;
+      acc.mf += (unsigned long long)d;
+    }
+    if (STATS) {
+      if (fnd) acc.edges += f0 ? 1ull : 2ull;
+      else if (!enq) acc.edges += (unsigned long long)d;
+    }
+    const unsigned em = __ballot_sync(kFull, enq);
+    if (enq) {
+      const int slot = np + __popc(em & lanemask_lt());
+      sm.pstart[slot] = (long long)h.z + 2;
+      sm.plen[slot] = d - 2;
+      sm.pv[slot] = v;
+      sm.pd[slot] = d;
+      sm.pex[slot] = 2;
+    }
+    np += __popc(em);
+    h = hn;
+    v = vn;
+    p0 = n0;
+    p1 = n1;
+    if (np >= kDrainMin) {
+      __syncwarp();
+      if (lane == 0) sm.npend = np;
+      bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
+      np = 0;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) sm.npend = np;
+  __syncwarp();
 }
 
 // One batch of 32 bitmap words (1024 vertices) of a bottom-up level, by one
-// warp.  The unvisited vertices of the batch are packed onto the lanes, two
-// per lane at a time; each looks for a frontier neighbour among the first
-// (aligned) four entries of its adjacency - one 128-bit load and four probes,
-// issued for both vertices before any result is used - and, if it has more
-// entries, is queued for bu_drain.  New-frontier bits are gathered in shared
-// memory and stored once per word, together with the updated visited word.
+// warp.  Each unvisited vertex looks for a frontier neighbour among its first
+// entries - the two of its head record (bu_head_batch), else the aligned four
+// of one 128-bit load - and, if it has more entries, becomes a deferred scan,
+// drained by the warp 32 at a time (bu_drain).  New-frontier bits are gathered
+// in shared memory and stored once per word, together with the updated
+// visited word.
 template <typename RP, bool STATS>
 __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* front, unsigned* next, long long w0,
                          unsigned vw, BuWarpSmem& sm, Acc& acc) {
@@ -752,93 +832,14 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
   const int total = __shfl_sync(kFull, incl, 31);
   if (STATS) acc.unvisited += (unsigned long long)cnt;
   __syncwarp();
-  const int nrounds = (total + 32 * kBuU - 1) / (32 * kBuU);
-
-  unsigned pw0[kBuU], pw1[kBuU];  // frontier words of the current round's two head neighbours
   if (P.head) {
-    // Prologue of the head pipeline: the records of rounds 0 .. kDepth-1 are
-    // requested now (one commit group per round, empty past the last round),
-    // then round 0's frontier words.
-#pragma unroll
-    for (int r = 0; r < kDepth; ++r) {
-      if (r < nrounds) bu_issue_round(P, sm, act, excl, total, w0, r, r);
-      cp_async_commit();
-    }
-    if (nrounds > 0) {
-      cp_async_wait<kDepth - 1>();
-      bu_probe_words(P, sm, front, 0, pw0, pw1);
-    }
-  }
-  for (int r = 0; r < nrounds; ++r) {
-    const int r0 = r * 32 * kBuU;
-    int v[kBuU];
-    if (P.head) {
-      // Head table: the first two neighbours (highest degree first under
-      // degree ordering), the list start and the degree in one 16-byte record.
-      // Three stages overlap: round r + kDepth's records are requested, round
-      // r + 1's frontier words are loaded, and round r is marked with the
-      // words loaded one round earlier.  Each lane reads only the slots it
-      // filled itself.
-      if (r + kDepth < nrounds) bu_issue_round(P, sm, act, excl, total, w0, r + kDepth, (r + kDepth) % kNBuf);
-      cp_async_commit();
-      unsigned nw0[kBuU] = {}, nw1[kBuU] = {};
-      if (r + 1 < nrounds) {
-        cp_async_wait<kDepth - 1>();
-        bu_probe_words(P, sm, front, (r + 1) % kNBuf, nw0, nw1);
-      }
-      const int buf = r % kNBuf;
-#pragma unroll
-      for (int k = 0; k < kBuU; ++k) v[k] = sm.vbuf[buf][32 * k + lane];
-      int4 hd[kBuU];
-#pragma unroll
-      for (int k = 0; k < kBuU; ++k) hd[k] = v[k] >= 0 ? sm.hbuf[buf][32 * k + lane] : make_int4(-1, -1, 0, 0);
-      unsigned f0[kBuU], f1[kBuU];
-#pragma unroll
-      for (int k = 0; k < kBuU; ++k) {
-        f0[k] = hd[k].x >= 0 ? ((pw0[k] >> (hd[k].x & 31)) & 1u) : 0u;
-        f1[k] = hd[k].y >= 0 ? ((pw1[k] >> (hd[k].y & 31)) & 1u) : 0u;
-        pw0[k] = nw0[k];
-        pw1[k] = nw1[k];
-      }
-      // The warp's pending queue and new-frontier words are its own: deferred
-      // vertices take slots by a ballot prefix count, and in a dense batch
-      // (round r = word r) the round's found vertices are word r's new bits.
-      const bool dense = total > 32 * 32 - 32;
-      int np = sm.npend;
-#pragma unroll
-      for (int k = 0; k < kBuU; ++k) {
-        const int d = hd[k].w;
-        const bool fnd = v[k] >= 0 && (f0[k] | f1[k]);
-        const bool enq = v[k] >= 0 && !(f0[k] | f1[k]) && d > 2;
-        const unsigned em = __ballot_sync(kFull, enq);
-        if (dense) {
-          const unsigned fm = __ballot_sync(kFull, fnd);
-          if (lane == 0 && fm) sm.next[(r0 >> 5) + k] |= fm;
-          if (fnd) {
-            mark_level(P, direct, v[k], L);
-            acc.found += 1;
-            acc.mf += (unsigned long long)d;
-          }
-        } else if (fnd) {
-          bu_mark_found(P, L, direct, sm, w0, v[k], d, acc);
-        }
-        if (STATS && fnd) acc.edges += f0[k] ? 1ull : 2ull;
-        if (enq) {
-          const int slot = np + __popc(em & lanemask_lt());
-          sm.pstart[slot] = (long long)hd[k].z + 2;
-          sm.plen[slot] = d - 2;
-          sm.pv[slot] = v[k];
-          sm.pd[slot] = d;
-          sm.pex[slot] = 2;
-        } else if (STATS && v[k] >= 0 && !fnd) {
-          acc.edges += (unsigned long long)d;
-        }
-        np += __popc(em);
-      }
-      __syncwarp();
-      if (lane == 0) sm.npend = np;
-    } else {
-      round_vertices(act, excl, total, w0, r0, v);
+    bu_head_batch<STATS>(P, L, direct, front, w0, act, excl, total, sm, acc);
+  } else {
+    // Row pointers and the aligned first four entries, one vertex per lane per round.
+    const int nrounds = (total + 31) / 32;
+    for (int r = 0; r < nrounds; ++r) {
+      int v[kBuU];
+      round_vertices(act, excl, total, w0, 32 * r, v);
       long long s[kBuU], e[kBuU];
 #pragma unroll
       for (int k = 0; k < kBuU; ++k) {
@@ -890,10 +891,11 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
           acc.edges += (unsigned long long)d;
         }
       }
+      __syncwarp();
+      if (sm.npend >= kDrainMin) bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
     }
-    __syncwarp();
-    if (sm.npend >= kDrainMin) bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
   }
+  __syncwarp();
   if (sm.npend > 0) bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
   __syncwarp();
   const unsigned nx = sm.next[lane];
