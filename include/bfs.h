@@ -313,6 +313,31 @@ int bfs_single_ex(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *pa
                   bfs_stats *stats, bfs_level_stat *levels, int32_t level_cap, void *stream);
 
 /*
+ * Enqueue one single-source query (as bfs_single_ex without statistics) and
+ * return without waiting for it, so that a caller with many queries keeps the
+ * device busy: the next query's launch is queued while this one runs.
+ *  dist   int32[n] device memory, or pinned host memory written through its
+ *         device alias (not under BFS_POLICY_LOCAL); owned by the caller and
+ *         written when the stream reaches the query.  Pageable host memory:
+ *         BFS_EINVAL (it would need a staged copy and a wait).
+ * Queries on one graph run in submission order on the device, whichever streams
+ * they name (they share its workspace), and each dist buffer is complete once
+ * its stream passes the query.  A query's device status (BFS_ETIMEOUT) is kept
+ * on the device until bfs_single_wait reports it.
+ * Returns BFS_OK once enqueued; BFS_EINVAL, BFS_ENOMEM, BFS_ECUDA.
+ */
+int bfs_single_async(bfs_graph *g, int32_t src, int32_t *dist, const bfs_params *params, void *stream);
+
+/*
+ * Wait until every single-source query enqueued on g has finished and return
+ * the first failed status (BFS_ETIMEOUT) among the queries since the previous
+ * wait (a failure already returned by a synchronous call is not repeated), or
+ * BFS_OK; the recorded status is then cleared.  BFS_OK at once if g has had no
+ * single-source query.  Errors: BFS_EINVAL (g NULL), BFS_ECUDA.
+ */
+int bfs_single_wait(bfs_graph *g);
+
+/*
  * Distances from k sources at once (multi-source BFS: the level-synchronous
  * loop of Section 2 run for up to 256 sources together, one bit per source in
  * per-vertex masks; sparse levels push as in Listing 1, dense levels pull as in

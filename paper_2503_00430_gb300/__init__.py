@@ -173,6 +173,8 @@ _SIGNATURES = [
     ("bfs_single", ctypes.c_int, [_vp, _i32, _vp, _vp]),
     ("bfs_single_ex", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_params), ctypes.POINTER(bfs_stats),
                                      _vp, _i32, _vp]),
+    ("bfs_single_async", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_params), _vp]),
+    ("bfs_single_wait", ctypes.c_int, [_vp]),
     ("bfs_single_noalloc", ctypes.c_int, [_vp, ctypes.c_int, _vp, _i64, _i64, _i32, _vp, _vp]),
     ("bfs_parents", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("bfs_single_nonatomic", ctypes.c_int, [_vp, _i32, _vp, ctypes.POINTER(bfs_dup_stats),
@@ -367,6 +369,20 @@ def bfs_single_ex(g: Graph, src: int, dist, params: bfs_params | None = None, st
             (i for i in range(level_cap) if lv[i].frontier == 0), level_cap)
         levels = [lv[i].as_dict() for i in range(nl)]
     return (st.as_dict() if st is not None else None), levels
+
+
+def bfs_single_async(g: Graph, src: int, dist, params: bfs_params | None = None, stream=None):
+    """Enqueue one single-source query without waiting (``dist``: device or pinned host
+    memory); ``bfs_single_wait`` reports a failed status of the queries since the last wait."""
+    _check(load().bfs_single_async(g.handle, int(src), _ptr(dist),
+                                   ctypes.byref(params) if params is not None else None, _stream_handle(stream)),
+           "bfs_single_async")
+    return dist
+
+
+def bfs_single_wait(g: Graph) -> None:
+    """Wait for g's enqueued single-source queries; raises BfsError with the first failed status."""
+    _check(load().bfs_single_wait(g.handle), "bfs_single_wait")
 
 
 def bfs_single_noalloc(row_ptr, col_idx, src: int, dist, stream=None):

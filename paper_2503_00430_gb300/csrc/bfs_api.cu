@@ -268,6 +268,8 @@ int ensure_single_ws(bfs_graph* g) {
   }
   GBFS_CUDA(cudaMalloc(&ws.ctrl, sizeof(Ctrl)));
   GBFS_CUDA(cudaMemset(ws.ctrl, 0, sizeof(Ctrl)));
+  GBFS_CUDA(cudaMalloc(&ws.sticky, sizeof(int)));
+  GBFS_CUDA(cudaMemset(ws.sticky, 0, sizeof(int)));
   GBFS_CUDA(cudaMallocHost(&ws.h_ctrl, sizeof(Ctrl)));
   GBFS_CUDA(cudaMallocHost(&ws.h_slot, sizeof(Slot)));
   GBFS_CUDA(cudaEventCreateWithFlags(&ws.done, cudaEventDisableTiming));
@@ -288,6 +290,7 @@ void free_single_ws(bfs_graph* g) {
     cudaFree(ws.mg[i]);
   }
   cudaFree(ws.ctrl);
+  cudaFree(ws.sticky);
   cudaFree(ws.dist_tmp);
   cudaFree(ws.lv8);
   cudaFree(ws.lst);
@@ -484,6 +487,49 @@ int bfs_single_ex(bfs_graph* g, int32_t src, int32_t* dist, const bfs_params* pa
 
 int bfs_single(bfs_graph* g, int32_t src, int32_t* dist, void* stream) {
   return bfs_single_ex(g, src, dist, nullptr, nullptr, nullptr, 0, stream);
+}
+
+int bfs_single_async(bfs_graph* g, int32_t src, int32_t* dist, const bfs_params* params, void* stream) {
+  GBFS_NVTX("bfs_single_async");
+  if (!g || !dist) return BFS_EINVAL;
+  if (src < 0 || (int64_t)src >= g->n) return BFS_EINVAL;
+  bfs_params p;
+  if (params) {
+    p = *params;
+  } else {
+    bfs_params_default(&p);
+  }
+  int rc = check_params(p);
+  if (rc != BFS_OK) return rc;
+  std::lock_guard<std::mutex> lock(g->mu);
+  rc = ensure_single_ws(g);
+  if (rc != BFS_OK) return rc;
+  if (p.relabel) {
+    rc = ensure_relabel_single(g);
+    if (rc != BFS_OK) return rc;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int* out = is_device_pointer(dist) ? dist : nullptr;
+  if (!out && !uses_local_kernel(g, p)) out = static_cast<int*>(pinned_device_alias(dist));
+  if (!out) return BFS_EINVAL;  // pageable host memory would need a staged copy and a wait
+  return run_single(g, src, out, p, nullptr, nullptr, 0, s, false);
+}
+
+int bfs_single_wait(bfs_graph* g) {
+  GBFS_NVTX("bfs_single_wait");
+  if (!g) return BFS_EINVAL;
+  std::lock_guard<std::mutex> lock(g->mu);
+  SingleWs& ws = g->ws;
+  if (!ws.ready) return BFS_OK;
+  GBFS_CUDA(cudaEventSynchronize(ws.done));
+  // Queries before the last one left their status in the sticky word (folded
+  // when the next query was enqueued); the last one's is still in the block.
+  int sticky = 0, last = 0;
+  GBFS_CUDA(cudaMemcpy(&sticky, ws.sticky, sizeof(int), cudaMemcpyDeviceToHost));
+  GBFS_CUDA(cudaMemcpy(&last, &ws.ctrl->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (sticky != 0) GBFS_CUDA(cudaMemset(ws.sticky, 0, sizeof(int)));
+  if (last != 0) GBFS_CUDA(cudaMemset(&ws.ctrl->status, 0, sizeof(int)));
+  return sticky != 0 ? sticky : last;
 }
 
 int bfs_multi_ex(bfs_graph* g, const int32_t* srcs, int32_t k, void* dist, int dist_bits, const bfs_params* params,

@@ -149,6 +149,7 @@ struct SingleWs {
   bfs_level_stat* lst = nullptr;
   int lst_cap = 0;
   cudaEvent_t done = nullptr;  // last query's completion on the device
+  int* sticky = nullptr;       // device: first failed status of a query since the last bfs_single_wait
   cudaGraph_t graph = nullptr;     // captured persistent launch (BFS_LAUNCH_GRAPH)
   cudaGraphNode_t knode = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -220,8 +221,15 @@ int ensure_relabel_single(bfs_graph* g);  // + head table, visited mask, host ne
 void free_relabel(bfs_graph* g);
 int ensure_single_ws(bfs_graph* g);
 void free_single_ws(bfs_graph* g);
+// One single-source query on the graph's workspace.  wait = false enqueues it
+// and returns (no statistics, no level records); its status then reaches the
+// workspace's sticky status when the next query is enqueued, or the next
+// bfs_single_wait reads it.
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
-               bfs_level_stat* levels, int level_cap, cudaStream_t stream);
+               bfs_level_stat* levels, int level_cap, cudaStream_t stream, bool wait = true);
+// Control-block reset before a single-source query (replaces a memset): the
+// previous query's status is folded into ws.sticky, then the block is zeroed.
+cudaError_t enqueue_ctrl_reset(SingleWs& ws, cudaStream_t stream);
 int run_nonatomic(bfs_graph* g, int src, int* dist, int mode, bfs_dup_stats* st, bfs_dup_level* lv, int lv_cap,
                   cudaStream_t s);
 void free_nonatomic_ws(NonAtomicWs* ws);

@@ -407,7 +407,7 @@ int run_local(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_sta
   if (p.blocks_per_sm > 0 && p.blocks_per_sm < per_sm) per_sm = p.blocks_per_sm;
   dim3 grid((unsigned)(per_sm * g->num_sms)), block((unsigned)threads);
   void* args[] = {&P};
-  GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
+  GBFS_CUDA(enqueue_ctrl_reset(ws, stream));
   GBFS_CUDA(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, stream));
   return BFS_OK;
 }

@@ -1518,6 +1518,26 @@ static int launch_per_level(bfs_graph* g, KParams& K, const bfs_params& p, cudaS
   return BFS_OK;
 }
 
+// Control-block reset before a query: the previous query's status (still in
+// the block) is kept in *sticky if no earlier failure is, then the block is
+// zeroed.  One block; the status is read before any word is cleared.
+__global__ void __launch_bounds__(128) k_ctrl_reset(Ctrl* c, int* sticky) {
+  static_assert(sizeof(Ctrl) % sizeof(unsigned long long) == 0, "control block of whole words");
+  constexpr int kWords = (int)(sizeof(Ctrl) / sizeof(unsigned long long));
+  if (threadIdx.x == 0) {
+    const int s = c->status;
+    if (s != 0 && *sticky == 0) *sticky = s;
+  }
+  __syncthreads();
+  unsigned long long* w = reinterpret_cast<unsigned long long*>(c);
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x) w[i] = 0ull;
+}
+
+cudaError_t enqueue_ctrl_reset(SingleWs& ws, cudaStream_t stream) {
+  k_ctrl_reset<<<1, 128, 0, stream>>>(ws.ctrl, ws.sticky);
+  return cudaGetLastError();
+}
+
 // The persistent launch (control-block reset + cooperative kernel) captured
 // once as a CUDA graph per workspace and replayed with refreshed arguments.
 template <typename RP>
@@ -1543,16 +1563,15 @@ static int launch_graph(bfs_graph* g, KParams& K, const bfs_params& p, cudaStrea
     ws.gexec = nullptr;
     ws.graph = nullptr;
     GBFS_CUDA(cudaGraphCreate(&ws.graph, 0));
-    cudaGraphNode_t memset_node;
-    cudaMemsetParams mp{};
-    mp.dst = ws.ctrl;
-    mp.value = 0;
-    mp.elementSize = 1;
-    mp.width = sizeof(Ctrl);
-    mp.height = 1;
-    mp.pitch = 0;
-    GBFS_CUDA(cudaGraphAddMemsetNode(&memset_node, ws.graph, nullptr, 0, &mp));
-    GBFS_CUDA(cudaGraphAddKernelNode(&ws.knode, ws.graph, &memset_node, 1, &kp));
+    cudaGraphNode_t reset_node;
+    cudaKernelNodeParams rp{};
+    rp.func = reinterpret_cast<void*>(&k_ctrl_reset);
+    rp.gridDim = dim3(1);
+    rp.blockDim = dim3(128);
+    void* rargs[] = {&ws.ctrl, &ws.sticky};
+    rp.kernelParams = rargs;
+    GBFS_CUDA(cudaGraphAddKernelNode(&reset_node, ws.graph, nullptr, 0, &rp));
+    GBFS_CUDA(cudaGraphAddKernelNode(&ws.knode, ws.graph, &reset_node, 1, &kp));
     cudaLaunchAttributeValue coop{};
     coop.cooperative = 1;
     GBFS_CUDA(cudaGraphKernelNodeSetAttribute(ws.knode, cudaLaunchAttributeCooperative, &coop));
@@ -1582,7 +1601,7 @@ int launch_persistent_prepared(KParams& K, int rp_bits, int num_sms, int threads
 }
 
 int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_stats* st,
-               bfs_level_stat* levels, int level_cap, cudaStream_t stream) {
+               bfs_level_stat* levels, int level_cap, cudaStream_t stream, bool wait) {
   SingleWs& ws = g->ws;
   KParams K;
   fill_kparams(g, src, dist_dev, p, K);
@@ -1605,7 +1624,7 @@ int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_st
   const bool local = K.policy == BFS_POLICY_LOCAL;
   if (local && launch == BFS_LAUNCH_PER_LEVEL) return BFS_EINVAL;
   if (launch == BFS_LAUNCH_GRAPH && stats) launch = BFS_LAUNCH_PERSISTENT;
-  if (launch != BFS_LAUNCH_GRAPH && !local) GBFS_CUDA(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
+  if (launch != BFS_LAUNCH_GRAPH && !local) GBFS_CUDA(enqueue_ctrl_reset(ws, stream));
   if (local) {
     rc = run_local(g, src, dist_dev, p, st, levels, level_cap, stream);
   } else if (launch == BFS_LAUNCH_GRAPH) {
@@ -1624,11 +1643,20 @@ int run_single(bfs_graph* g, int src, int* dist_dev, const bfs_params& p, bfs_st
                  : launch_persistent<long long, false>(g, K, p, stream);
   }
   if (rc != BFS_OK) return rc;
+  if (!wait) {
+    GBFS_CUDA(cudaEventRecord(ws.done, stream));
+    return BFS_OK;
+  }
   GBFS_CUDA(cudaMemcpyAsync(ws.h_ctrl, ws.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream));
   GBFS_CUDA(cudaEventRecord(ws.done, stream));
   GBFS_CUDA(cudaStreamSynchronize(stream));
   const Ctrl& c = *ws.h_ctrl;
-  if (c.status != 0) return c.status;
+  if (c.status != 0) {
+    // Returned here: cleared, so that the next query's reset does not keep it
+    // for bfs_single_wait as well.
+    GBFS_CUDA(cudaMemset(&ws.ctrl->status, 0, sizeof(int)));
+    return c.status;
+  }
   if (st) {
     st->levels = c.levels;
     st->td_levels = c.td_levels;
