@@ -5,10 +5,12 @@
 // paper's hybrid BFS (Section 2, Listing 2 with Listing 3's visited bitmap) on
 // one graph at a time, entirely inside the block: the visited, frontier and
 // next-frontier bitmaps live in shared memory and __syncthreads() is the level
-// barrier.  Top-down levels expand the set bits of the frontier bitmap (one
-// lane per frontier vertex, claims by shared-memory atomicOr); bottom-up
-// levels give each warp 32 consecutive vertices that scan for a frontier
-// neighbour and stop at the first one.  The direction follows the edge-count
+// barrier.  Top-down levels expand the frontier bitmap a word per warp: the
+// lists of the word's frontier vertices are concatenated and dealt to the
+// lanes 32 entries per step (claims by shared-memory atomicOr); bottom-up
+// levels give each warp 32 consecutive vertices that scan their lists in
+// aligned 128-bit groups of four entries for a frontier neighbour and stop at
+// the first one.  The direction follows the edge-count
 // rule with the graph's own counters.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,6 +22,7 @@
 #include <vector>
 
 #include "bfs_internal.cuh"
+#include "bfs_device.cuh"
 
 struct bfs_graphset {
   int count = 0;
@@ -74,7 +77,8 @@ __global__ void __launch_bounds__(512) k_graphset(GsArgs A) {
     const long long vb = A.voff[gi];
     const int n = (int)(A.voff[gi + 1] - vb);
     const long long* rp = A.rp + vb + gi;
-    const int* col = A.col + A.eoff[gi];
+    const long long cbase = A.eoff[gi];
+    const int* col = A.col + cbase;
     int* dist = A.dist + vb;
     const int src = A.src[gi];
     const long long m = A.eoff[gi + 1] - A.eoff[gi];
@@ -107,22 +111,37 @@ __global__ void __launch_bounds__(512) k_graphset(GsArgs A) {
       __syncthreads();
       unsigned long long my_nf = 0, my_mf = 0;
       if (td) {
-        // One warp per frontier word, one lane per set bit.
+        // One warp per frontier word: the lists of the word's frontier vertices
+        // are concatenated (exclusive scan of their lengths) and dealt to the
+        // lanes 32 entries per step, so a step issues its neighbour loads
+        // together instead of one list walk per lane.
         for (int w = (int)warp; w < nw; w += (int)nwarp) {
           const unsigned word = front[w];
           if (!word) continue;
+          long long s = 0;
+          int len = 0;
           if ((word >> lane) & 1u) {
             const int u = 32 * w + (int)lane;
-            for (long long j = rp[u]; j < rp[u + 1]; ++j) {
-              const int v = __ldg(col + j);
-              const unsigned bit = 1u << (v & 31);
-              if (vis[v >> 5] & bit) continue;
-              if (atomicOr(&vis[v >> 5], bit) & bit) continue;
-              dist[v] = L + 1;
-              atomicOr(&next[v >> 5], bit);
-              my_nf += 1;
-              my_mf += (unsigned long long)(rp[v + 1] - rp[v]);
-            }
+            s = rp[u];
+            len = (int)(rp[u + 1] - s);
+          }
+          const int incl = dev::warp_incl_scan(len);
+          const int excl = incl - len;
+          const int total = __shfl_sync(0xffffffffu, incl, 31);
+          for (int base = 0; base < total; base += 32) {
+            const int e = base + (int)lane;
+            const int o = dev::owner_of(excl, e);
+            const long long so = __shfl_sync(0xffffffffu, s, o);
+            const int eo = __shfl_sync(0xffffffffu, excl, o);
+            if (e >= total) continue;
+            const int v = __ldg(col + so + (e - eo));
+            const unsigned bit = 1u << (v & 31);
+            if (vis[v >> 5] & bit) continue;
+            if (atomicOr(&vis[v >> 5], bit) & bit) continue;
+            dist[v] = L + 1;
+            atomicOr(&next[v >> 5], bit);
+            my_nf += 1;
+            my_mf += (unsigned long long)(rp[v + 1] - rp[v]);
           }
         }
       } else {
@@ -136,12 +155,15 @@ __global__ void __launch_bounds__(512) k_graphset(GsArgs A) {
           if (!((vw >> lane) & 1u)) {
             const long long s = rp[v], e = rp[v + 1];
             d = e - s;
-            for (long long j = s; j < e; ++j) {
-              const int u = __ldg(col + j);
-              if ((front[u >> 5] >> (u & 31)) & 1u) {
-                found = true;
-                break;
-              }
+            // Aligned groups of four entries of the whole column array (16-byte
+            // aligned, 4 spare entries past the last list), masked to [s, e).
+            const long long gs = cbase + s, ge = cbase + e;
+            for (long long a = gs & ~3ll; a < ge && !found; a += 4) {
+              const int4 q = __ldg(reinterpret_cast<const int4*>(A.col + a));
+              const int c4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (a + t >= gs && a + t < ge && ((front[c4[t] >> 5] >> (c4[t] & 31)) & 1u)) found = true;
             }
           }
           const unsigned fm = __ballot_sync(0xffffffffu, found);

@@ -61,8 +61,10 @@ def test_parameters(bfs, kw):
 
 def test_mixed_shapes(bfs):
     graphs = [G.path_graph(1), G.path_graph(300), G.star_graph(70), G.complete_graph(40), G.cycle_graph(1001),
-              graphgen.grid2d(40, 33), graphgen.rmat(12, seed=5), G.csr_from_edges(64, [(0, 1), (5, 6)])]
-    srcs = np.array([0, 150, 3, 7, 500, 600, int(graphgen.sources(graphs[6][0], 1, 3)[0]), 5], dtype=np.int32)
+              graphgen.grid2d(40, 33), graphgen.rmat(12, seed=5), G.csr_from_edges(64, [(0, 1), (5, 6)]),
+              G.star_graph(5000), graphgen.rmat(14, seed=2)]  # long lists: many 32-entry steps per frontier word
+    srcs = np.array([0, 150, 3, 7, 500, 600, int(graphgen.sources(graphs[6][0], 1, 3)[0]), 5, 17,
+                     int(graphgen.sources(graphs[9][0], 1, 4)[0])], dtype=np.int32)
     check_set(bfs, *concat(graphs), srcs, graphs)
 
 
