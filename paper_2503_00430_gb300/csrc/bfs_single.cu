@@ -507,6 +507,7 @@ __device__ void td_phase(const KParams& P, int L, bool direct, unsigned long lon
 constexpr int kBuU = 1;  // unvisited vertices per lane in a bottom-up round
 constexpr int kDrainMin = GBFS_DRAIN_MIN;  // deferred scans that trigger a drain within a batch
 constexpr int kPendCap = 32 * kBuU + kDrainMin - 1;  // deferred long scans per warp
+static_assert(kDrainMin <= 32, "a drain of one group leaves fewer than 32 scans behind");
 constexpr int kNBuf = 3;  // ring slots of head records in flight
 struct BuWarpSmem {
   int4 hbuf[kNBuf][32 * kBuU];   // head records of the rounds in flight (lane-private slots)
@@ -534,10 +535,14 @@ __device__ __forceinline__ void bu_mark_found(const KParams& P, int L, bool dire
 // vertex's remaining entries are skipped once it has found a parent.  Ranges
 // longer than bu_warp_min are scanned one at a time by the whole warp.
 template <bool STATS>
-__device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* front, BuWarpSmem& sm, long long w0, Acc& acc) {
+__device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* front, BuWarpSmem& sm, long long w0, Acc& acc,
+                         bool one_group = false) {
   const unsigned lane = lane_id();
   __syncwarp();
-  const int np = sm.npend;
+  const int np_all = sm.npend;
+  // one_group: only the first 32 are scanned (a full group of lanes); the
+  // rest move to the front of the queue and wait for the next drain.
+  const int np = one_group && np_all > 32 ? 32 : np_all;
   for (int g0 = 0; g0 < np; g0 += 32) {
     const int j = g0 + (int)lane;
     const bool have = j < np;
@@ -665,7 +670,15 @@ __device__ void bu_drain(const KParams& P, int L, bool direct, const unsigned* f
     if (STATS && have) acc.edges += (unsigned long long)ex;
   }
   __syncwarp();
-  if (lane == 0) sm.npend = 0;
+  const int rest = np_all - np;  // < 32: records np .. np_all-1 move to 0 .. rest-1 (no overlap)
+  if ((int)lane < rest) {
+    sm.pstart[lane] = sm.pstart[np + lane];
+    sm.plen[lane] = sm.plen[np + lane];
+    sm.pv[lane] = sm.pv[np + lane];
+    sm.pd[lane] = sm.pd[np + lane];
+    sm.pex[lane] = sm.pex[np + lane];
+  }
+  if (lane == 0) sm.npend = rest;
   __syncwarp();
 }
 
@@ -803,8 +816,8 @@ __device__ __forceinline__ void bu_head_batch(const KParams& P, int L, bool dire
     if (np >= kDrainMin) {
       __syncwarp();
       if (lane == 0) sm.npend = np;
-      bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
-      np = 0;
+      bu_drain<STATS>(P, L, direct, front, sm, w0, acc, true);
+      np = sm.npend;
     }
   }
   __syncwarp();
@@ -892,7 +905,7 @@ __device__ void bu_batch(const KParams& P, int L, bool direct, const unsigned* f
         }
       }
       __syncwarp();
-      if (sm.npend >= kDrainMin) bu_drain<STATS>(P, L, direct, front, sm, w0, acc);
+      if (sm.npend >= kDrainMin) bu_drain<STATS>(P, L, direct, front, sm, w0, acc, true);
     }
   }
   __syncwarp();
