@@ -103,3 +103,14 @@ def test_msbfs_bytes_hand_worked():
 def test_graphset_bytes():
     # 3 graphs, 10 vertices, 40 entries: 8 * (10 + 3) row pointers + 4 * 40 list + 4 * 10 distances
     assert bench.graphset_bytes(10, 40, 3) == 104 + 160 + 40
+
+
+def test_launches_per_query_counts_the_reset_and_the_levels():
+    """gpu_launches claims two launches per query (control-block reset + one persistent, graph or
+    local kernel); with one launch per level: reset, init, every level, two per direction change
+    (the worst case: zeroing + scatter), final expansion."""
+    from types import SimpleNamespace
+    per_src = [{"stats": {"levels": 7, "conversions": 2}}, {"stats": {"levels": 9, "conversions": 0}}]
+    for launch in (0, 2):
+        assert bench.launches_per_query(SimpleNamespace(launch=launch), per_src) == 4
+    assert bench.launches_per_query(SimpleNamespace(launch=1), per_src) == (3 + 7 + 4) + (3 + 9)
